@@ -1,0 +1,169 @@
+/*
+ * oracle.h -- plain single-threaded FP64 CPU oracle of the VEGAS / BASES
+ * iteration described in Sec. 2.1 of "Monte Carlo integration on GPU"
+ * (Kanzaki, arXiv 1010.2107): steps 2 (point generation), 3 (integrand),
+ * 4 (accumulation), 5 (grid optimisation) and 6 (iteration / stopping),
+ * plus the BASES two-phase split of Sec. 2.1 and Sec. 5.1.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA library
+ * against.  Only the test suite, the package entry's smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant with the CUDA library and never calls it.
+ *
+ * Precision: every value is computed in IEEE binary64 (double); sums use
+ * Neumaier-compensated accumulation.  Built with -ffp-contract=off so that
+ * x86-64 and aarch64 give identical results.
+ *
+ * Parity unpinned: the full RAMBO integrand with its cuts (kind 5, obs 0)
+ * has no closed form.  Its building blocks are pinned (phase-space volume,
+ * momentum conservation, <s12>, the s12 density, hand-built cut cases and
+ * Lorentz / azimuthal invariances) but the complete product is checked
+ * only against the CUDA path and by statistical consistency.
+ */
+#ifndef GVEGAS_ORACLE_H
+#define GVEGAS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXDIM 64
+#define ORC_MAXBINS 1024
+
+/* Integrand kinds.  The numbering is a convention that the test suite maps
+ * to the CUDA library's own enumeration. */
+enum {
+  ORC_GENZ_GAUSSIAN = 0,     /* params: a[d], u[d]                          */
+  ORC_GENZ_PRODUCT_PEAK = 1, /* params: a[d], u[d]                          */
+  ORC_GENZ_CORNER_PEAK = 2,  /* params: a[d]                                */
+  ORC_GENZ_OSCILLATORY = 3,  /* params: a[d], u1                            */
+  ORC_DOUBLE_GAUSSIAN = 4,   /* params: c1, c2, w                           */
+  ORC_RAMBO_BW = 5           /* params: see ORC_RB_* below, d = 4 n         */
+};
+
+/* RAMBO + Breit-Wigner parameter slots. */
+enum {
+  ORC_RB_N = 0,      /* number of massless final-state partons n >= 2     */
+  ORC_RB_SQRTS = 1,  /* partonic centre-of-mass energy, GeV              */
+  ORC_RB_M = 2,      /* Breit-Wigner mass, GeV                           */
+  ORC_RB_GAMMA = 3,  /* Breit-Wigner width, GeV                          */
+  ORC_RB_PTMIN = 4,  /* hard transverse-momentum cut, GeV                */
+  ORC_RB_DRMIN = 5,  /* Delta R separation cut                           */
+  ORC_RB_CUT = 6,    /* 0 hard pT cut, 1 sigmoid pT cut, 2 no cuts       */
+  ORC_RB_T = 7,      /* sigmoid threshold, GeV                           */
+  ORC_RB_WC = 8,     /* sigmoid width, GeV                               */
+  ORC_RB_OBS = 9,    /* 0 full integrand, 1 unit, 2 s12, 3 BW(s12) only  */
+  ORC_RB_NPARAMS = 10
+};
+
+typedef struct {
+  int kind;
+  int ndim;
+  const double* params;
+  int nparams;
+} orc_fn;
+
+/* One VEGAS / BASES context: NCALL points per iteration in ndim
+ * dimensions, nbins grid bins per axis, nstrat hypercube divisions per
+ * axis (0 or 1 = no stratification), ybits = 24 (one Philox word per axis)
+ * or 53 (two words per axis). */
+typedef struct {
+  int ndim;
+  int nbins;
+  int64_t ncall;
+  int nstrat;
+  int ybits;
+  uint64_t seed;
+  uint32_t instance;
+  double alpha;
+} orc_cfg;
+
+/* Per-iteration outputs.  S1, S2: [ndim][nbins]; C1, C2: [nstrat^ndim]
+ * (may be NULL).  tot: {sum w, sum w^2, I_j, sigma_j^2}. */
+typedef struct {
+  double* S1;
+  double* S2;
+  double* C1;
+  double* C2;
+  double tot[4];
+  int64_t nonfinite;
+} orc_iter_out;
+
+/* Philox4x32-10 block: out = Philox(ctr, key). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+
+/* The random words of sample s in iteration it (ndim or 2 ndim words). */
+int orc_sample_words(const orc_cfg* cfg, uint32_t it, uint64_t s,
+                     uint32_t* words);
+
+/* Step 2: bins[a], frac[a], x[a] and the Jacobian of sample s. */
+int orc_sample_point(const orc_cfg* cfg, const double* edges, uint32_t it,
+                     uint64_t s, int32_t* bins, double* frac, double* x,
+                     double* jac);
+
+/* Step 2 from given words: the point of a sample in hypercube `cube`. */
+int orc_point_from_words(const orc_cfg* cfg, const double* edges,
+                         uint64_t cube, const uint32_t* words, int32_t* bins,
+                         double* frac, double* x, double* jac);
+int orc_points_from_words(const orc_cfg* cfg, const double* edges,
+                          const uint64_t* cube, const uint32_t* words,
+                          int64_t n, int32_t* bins, double* frac, double* x,
+                          double* jac);
+
+/* Step 2 for a list of sample indices; any output pointer may be NULL.
+ * words: [n][W], bins: [n][ndim], frac, x: [n][ndim], jac: [n]. */
+int orc_sample_batch(const orc_cfg* cfg, const double* edges, uint32_t it,
+                     const uint64_t* s, int64_t n, uint32_t* words,
+                     int32_t* bins, double* frac, double* x, double* jac);
+
+/* Step 3: the integrand at n points x[n][ndim]. */
+int orc_integrand(const orc_fn* fn, int64_t n, const double* x, double* f);
+
+/* d f / d theta at n points; theta = (M, Gamma, T) for RAMBO_BW and
+ * (u[d], a[d]) for GENZ_GAUSSIAN.  grad: [n][ntheta]. */
+int orc_integrand_grad(const orc_fn* fn, int64_t n, const double* x,
+                       double* grad);
+int orc_ntheta(const orc_fn* fn);
+
+/* RAMBO: n massless momenta (E, px, py, pz) from 4n numbers in (0, 1]. */
+int orc_rambo(int n, double sqrt_s, const double* rho, double* p);
+/* The RAMBO_BW integrand without the phase-space weight, from momenta. */
+double orc_rambo_f_momenta(const double* params, const double* p);
+/* Phase-space volume of n massless particles at energy sqrt_s. */
+double orc_rambo_volume(int n, double sqrt_s);
+
+/* Step 4: one full iteration over NCALL points. */
+int orc_iteration(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
+                  uint32_t it, orc_iter_out* out);
+
+/* Step 5: grid optimisation from the per-bin sums of squares. */
+int orc_refine(int ndim, int nbins, double alpha, const double* S2,
+               double* edges);
+
+/* Step 6: combination of m iteration estimates.  out = {I, sigma, chi2/dof}. */
+void orc_combine(int m, const double* I, const double* var, double out[3]);
+
+/* VEGAS loop: up to itmx iterations starting at Philox iteration it0,
+ * refining after each if refine != 0, stopping when sigma/|I| < acc.
+ * hist: [itmx][2] (I_j, sigma_j^2).  Returns the number of iterations run. */
+int orc_vegas(const orc_cfg* cfg, const orc_fn* fn, double* edges,
+              uint32_t it0, int itmx, int refine, double acc, double* hist,
+              double out[3]);
+
+/* BASES: phase 1 (itmx1 iterations, refining) then phase 2 (itmx2
+ * iterations, frozen grid); out combines phase 2 only.  n_done: {n1, n2}. */
+int orc_bases(const orc_cfg* cfg, const orc_fn* fn, double* edges,
+              uint32_t it0, int itmx1, double acc1, int itmx2, double acc2,
+              double* hist, double out[3], int n_done[2]);
+
+/* Estimator gradient on a frozen grid: dI/dtheta = (1/n) sum J df/dtheta. */
+int orc_gradient(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
+                 uint32_t it, double* grad, double* I);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

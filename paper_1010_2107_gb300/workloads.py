@@ -1,0 +1,118 @@
+"""Seeded synthetic workloads: shapes, sizes and integrand parameter vectors.
+
+This module holds no arithmetic of the integration method.  It only states the
+five workloads (sizes, seeds, parameter vectors) and draws the parameters of the
+batched Genz workload from numpy's PCG64 generator.  Both the CUDA library's
+callers and the CPU oracle's tests take their inputs from here.
+
+Workloads (after Sec. 5.1's conventions: NCALL points per iteration, ITMX
+iterations, BASES split ITMX1 = ITMX2 with ITMX1 + ITMX2 = ITMX):
+
+* ``gauss4``   VEGAS, FP64, d=4 Genz Gaussian exp(-sum 100 (x_i - 0.5)^2),
+               50 bins, 5 iterations x 1e5 points, seed 1.
+* ``dgauss8``  BASES, hypercube-stratified (4 divisions per axis, 65 536 cubes
+               x 64 points), FP32 integrand, d=8 two-peak Gaussian (centres
+               1/3 and 2/3, width 0.05), 50 bins, 5 + 5 iterations x 2^22.
+* ``rambo5``   VEGAS on massless 2->5 RAMBO phase space at sqrt(s) = 1 TeV
+               (20 dims), cyclic 1/s_{i,i+1} x Breit-Wigner(s12), pT > 20 GeV
+               and Delta R > 0.4 cuts, FP32, 12 iterations x 2^24.
+* ``rambo4_adjoint``  2->4 RAMBO (16 dims), sigmoid pT cut (T = 20 GeV,
+               width 1 GeV); gradient in (M, Gamma, T) on 2^24 points after a
+               5-iteration grid warm-up.
+* ``genz256``  256 Genz integrands (product peak, corner peak, oscillatory),
+               d uniform in 2..16, points per instance log-uniform in
+               2^16..2^22, 8 iterations each.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Integrand kinds, in the numbering of include/gvegas.h.
+GENZ_GAUSSIAN = 0
+GENZ_PRODUCT_PEAK = 1
+GENZ_CORNER_PEAK = 2
+GENZ_OSCILLATORY = 3
+DOUBLE_GAUSSIAN = 4
+RAMBO_BW = 5
+
+# Parameter slots of RAMBO_BW.
+RB_N, RB_SQRTS, RB_M, RB_GAMMA, RB_PTMIN, RB_DRMIN, RB_CUT, RB_T, RB_WC, RB_OBS = range(10)
+RB_NPARAMS = 10
+
+# Genz "difficulty" sums sum_i a_i per family (values customary in the
+# Genz test-function literature).
+GENZ_DIFFICULTY = {GENZ_OSCILLATORY: 9.0, GENZ_PRODUCT_PEAK: 7.25,
+                   GENZ_CORNER_PEAK: 1.85}
+
+
+def genz_gaussian_params(d: int, a: float = 10.0, u: float = 0.5) -> np.ndarray:
+    """[a_1..a_d, u_1..u_d] for f = exp(-sum a_i^2 (x_i - u_i)^2)."""
+    return np.concatenate([np.full(d, a), np.full(d, u)]).astype(np.float64)
+
+
+def double_gaussian_params(c1: float = 1.0 / 3.0, c2: float = 2.0 / 3.0,
+                           w: float = 0.05) -> np.ndarray:
+    return np.array([c1, c2, w], dtype=np.float64)
+
+
+def rambo_params(n: int, sqrt_s: float = 1000.0, M: float = 80.4,
+                 Gamma: float = 2.1, ptmin: float = 20.0, drmin: float = 0.4,
+                 cut: int = 0, T: float = 20.0, wc: float = 1.0,
+                 obs: int = 0) -> np.ndarray:
+    p = np.zeros(RB_NPARAMS)
+    p[RB_N], p[RB_SQRTS], p[RB_M], p[RB_GAMMA] = n, sqrt_s, M, Gamma
+    p[RB_PTMIN], p[RB_DRMIN], p[RB_CUT] = ptmin, drmin, cut
+    p[RB_T], p[RB_WC], p[RB_OBS] = T, wc, obs
+    return p
+
+
+WORKLOADS = {
+    "gauss4": dict(kind=GENZ_GAUSSIAN, ndim=4, params=genz_gaussian_params(4),
+                   nbins=50, ncall=100_000, itmx=5, nstrat=0, seed=1,
+                   precision="fp64", ybits=53, mode="vegas"),
+    "dgauss8": dict(kind=DOUBLE_GAUSSIAN, ndim=8, params=double_gaussian_params(),
+                    nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,
+                    precision="fp32", ybits=24, mode="bases"),
+    "rambo5": dict(kind=RAMBO_BW, ndim=20, params=rambo_params(5), nbins=50,
+                   ncall=1 << 24, itmx=12, nstrat=0, seed=1, precision="fp32",
+                   ybits=24, mode="vegas"),
+    "rambo4_adjoint": dict(kind=RAMBO_BW, ndim=16, params=rambo_params(4, cut=1),
+                           nbins=50, ncall=1 << 24, warmup_iters=5, nstrat=0,
+                           seed=1, precision="fp32", ybits=24, mode="adjoint"),
+}
+
+
+def genz_batch(count: int = 256, seed: int = 2, dmin: int = 2, dmax: int = 16,
+               log2n_min: float = 16.0, log2n_max: float = 22.0):
+    """Parameters of `count` Genz integrands drawn from PCG64(seed).
+
+    Returns a list of dicts with kind, ndim, ncall and the parameter vector in
+    the layout of include/gvegas.h:
+      product peak: a[d], u[d];  corner peak: a[d];  oscillatory: a[d], u_1.
+    a_i are uniform draws rescaled so that sum_i a_i equals the family's
+    difficulty; u_i are uniform in [0, 1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    families = (GENZ_PRODUCT_PEAK, GENZ_CORNER_PEAK, GENZ_OSCILLATORY)
+    out = []
+    for i in range(count):
+        kind = families[int(rng.integers(0, 3))]
+        d = int(rng.integers(dmin, dmax + 1))
+        n = int(math.floor(2.0 ** (log2n_min + (log2n_max - log2n_min) * rng.random())))
+        a = rng.random(d)
+        a = a * (GENZ_DIFFICULTY[kind] / a.sum())
+        u = rng.random(d)
+        if kind == GENZ_PRODUCT_PEAK:
+            params = np.concatenate([a, u])
+        elif kind == GENZ_CORNER_PEAK:
+            params = a.copy()
+        else:
+            params = np.concatenate([a, u[:1]])
+        out.append(dict(instance=i, kind=kind, ndim=d, ncall=n,
+                        params=params.astype(np.float64)))
+    return out
+
+
+GENZ256 = dict(count=256, seed=2, nbins=50, itmx=8, sample_seed=1,
+               precision="fp32", ybits=24, mode="batched")
