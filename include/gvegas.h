@@ -1,0 +1,240 @@
+/*
+ * gvegas.h -- C ABI of the GB300 (sm_103a) VEGAS / BASES library.
+ *
+ * The library runs the per-iteration loop of "Monte Carlo integration on
+ * GPU" (Kanzaki, arXiv 1010.2107), Sec. 2.1 steps 2-6, entirely on one GPU:
+ *   step 2  point generation (counter-based Philox4x32-10 in registers,
+ *           integer-exact grid bins, the adaptive-grid map x = g(y), J),
+ *   step 3  the integrand (a fixed registry: Genz families, two-peak
+ *           Gaussian, massless RAMBO phase space with a Breit-Wigner),
+ *   step 4  accumulation of w = f J into per-bin sums of w and w^2 on every
+ *           axis, per-hypercube sums (BASES), and the iteration estimate,
+ *   step 5  grid optimisation (smoothing, log-compression, rebinning) in FP64,
+ *   step 6  inverse-variance combination of iterations, chi^2, ACC test.
+ * The paper moved only steps 2-3 to the GPU and copied NCALL function values
+ * back every iteration (Sec. 2.2); here nothing but the small result
+ * structure crosses to the host, and only when asked.
+ *
+ * Conventions
+ *  - Every entry point returns a vegas_status; no exception or abort crosses
+ *    the ABI.  On failure vegas_last_error(ctx) (or vegas_last_error(NULL)
+ *    for failures before a context exists) gives a message.
+ *  - The context owns every device buffer it uses (cudaMalloc at creation,
+ *    cudaFree at vegas_destroy).  All pointers passed in or out are HOST
+ *    pointers owned by the caller, unless an argument says "device".
+ *  - Work is ordered on the context's CUDA stream (config.stream, or a
+ *    stream the context creates when that is NULL).  Calls that fill host
+ *    outputs synchronise that stream before returning; the others do not.
+ *  - The integration domain is the unit hypercube [0,1)^ndim.
+ *  - A context is not thread-safe: one host thread at a time.
+ *
+ * Random numbers: the j-th random word of sample s (0 <= s < NCALL) in
+ * iteration `it` of instance `inst` is output word j mod 4 of
+ * Philox4x32-10(counter = (s, floor(j/4), it, inst), key = (seed mod 2^32,
+ * seed >> 32)).  `it` counts every iteration the context has run, from 0.
+ * With ybits = 24 axis a uses word a (y_a = (word >> 8) / 2^24); with
+ * ybits = 53 it uses words 2a and 2a+1 (27 + 26 bits).  Grid bins are
+ * computed from those bits in integer arithmetic, so they do not depend on
+ * the floating-point precision of the rest of the path.
+ */
+#ifndef GVEGAS_H
+#define GVEGAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GVEGAS_MAXDIM 32      /* largest ndim a context accepts            */
+#define GVEGAS_MAXBINS 256    /* largest nbins (grid bins per axis)         */
+#define GVEGAS_MAXHIST 4096   /* iterations kept in one combination window  */
+
+typedef struct vegas_ctx vegas_ctx;
+
+typedef enum {
+  VEGAS_OK = 0,
+  VEGAS_EINVAL = 1,     /* an argument is out of range                      */
+  VEGAS_ENOMEM = 2,     /* a device or pinned-host allocation failed        */
+  VEGAS_ECUDA = 3,      /* a CUDA call failed (message has the CUDA error)  */
+  VEGAS_ETIMEOUT = 4,   /* a bounded device-side wait gave up               */
+  VEGAS_ENONFINITE = 5, /* reserved: non-finite weights are counted, not fatal */
+  VEGAS_ESTATE = 6      /* call not valid for this context (e.g. batch ctx) */
+} vegas_status;
+
+/* Integrand registry (step 3).  Parameter layouts, with d = ndim:
+ *  VG_GENZ_GAUSSIAN      a[d], u[d]:  f = exp(-sum_i a_i^2 (x_i - u_i)^2)
+ *  VG_GENZ_PRODUCT_PEAK  a[d], u[d]:  f = prod_i (a_i^-2 + (x_i - u_i)^2)^-1
+ *  VG_GENZ_CORNER_PEAK   a[d]:        f = (1 + sum_i a_i x_i)^-(d+1)
+ *  VG_GENZ_OSCILLATORY   a[d], u1:    f = cos(2 pi u1 + sum_i a_i x_i)
+ *  VG_DOUBLE_GAUSSIAN    c1, c2, w:   f = 1/2 sum_{c in {c1,c2}}
+ *                                          (w sqrt pi)^-d exp(-sum_i ((x_i-c)/w)^2)
+ *  VG_RAMBO_BW           10 slots (VG_RB_*), d = 4 n:  n massless partons
+ *      from RAMBO (4 numbers each), f = V_n * cut(p) * BW(s_12) *
+ *      prod_{i} 1/s_{i,i+1 mod n}, with BW(s) = M G / ((s-M^2)^2 + M^2 G^2),
+ *      V_n = (pi/2)^(n-1) s^(n-2) / ((n-1)!(n-2)!), cut = hard pT > ptmin
+ *      or prod_i sigmoid((pT_i - T)/wc), and Delta R_ij > drmin for all
+ *      pairs.  Units GeV.  (Stand-in for the W + n-gluon processes of
+ *      Sec. 4, eq. 1, with the jet cuts of eqs. 2-3.) */
+typedef enum {
+  VG_GENZ_GAUSSIAN = 0,
+  VG_GENZ_PRODUCT_PEAK = 1,
+  VG_GENZ_CORNER_PEAK = 2,
+  VG_GENZ_OSCILLATORY = 3,
+  VG_DOUBLE_GAUSSIAN = 4,
+  VG_RAMBO_BW = 5
+} vegas_integrand_kind;
+
+enum {
+  VG_RB_N = 0, VG_RB_SQRTS = 1, VG_RB_M = 2, VG_RB_GAMMA = 3,
+  VG_RB_PTMIN = 4, VG_RB_DRMIN = 5,
+  VG_RB_CUT = 6,   /* 0 hard pT cut, 1 sigmoid pT cut, 2 no cuts          */
+  VG_RB_T = 7, VG_RB_WC = 8,
+  VG_RB_OBS = 9,   /* 0 full integrand, 1 f = 1, 2 f = s12, 3 f = BW(s12) */
+  VG_RB_NPARAMS = 10
+};
+
+/* Arithmetic of the hot path.  Grid refinement and the combination of
+ * iterations are FP64 in every form.
+ *  VG_FP64          map, integrand and sums in FP64.
+ *  VG_FP32_ACC64    map and integrand in FP32; every weight is added to
+ *                   FP64 sums (per-bin histograms, totals, cube sums).
+ *  VG_FP32_ACCCOMP  map and integrand in FP32; per-thread and per-warp sums
+ *                   in compensated FP32 (hi, lo) pairs, per-bin histograms
+ *                   in FP32 shared memory flushed into FP64 every few
+ *                   thousand points; FP64 from the CTA level up. */
+typedef enum {
+  VG_FP64 = 0,
+  VG_FP32_ACC64 = 1,
+  VG_FP32_ACCCOMP = 2
+} vegas_precision;
+
+typedef struct {
+  int kind;              /* vegas_integrand_kind                          */
+  int ndim;              /* must equal vegas_config.ndim                  */
+  const double* params;  /* host array, copied at creation                */
+  int nparams;
+} vegas_integrand;
+
+/* Sec. 5.1 parameters (NCALL, ITMX, ACC) plus the grid and the sampler. */
+typedef struct {
+  int ndim;              /* 1..GVEGAS_MAXDIM                               */
+  int nbins;             /* grid bins per axis N, 2..GVEGAS_MAXBINS (50)   */
+  int64_t ncall;         /* points per iteration NCALL, 2..2^32            */
+  int itmx;              /* default iteration count for bases/iterate (>0) */
+  double acc;            /* stop when sigma/|I| < acc (<= 0: never)        */
+  double alpha;          /* grid damping exponent (1.5)                    */
+  int nstrat;            /* hypercube divisions per axis g; 0/1 = none.
+                            NCALL must be a multiple of g^ndim with at
+                            least 2 points per cube.                       */
+  uint64_t seed;         /* Philox key                                     */
+  uint32_t instance;     /* Philox counter word 3                          */
+  int precision;         /* vegas_precision                                */
+  int ybits;             /* 24 or 53; 0 = 53 for VG_FP64, 24 otherwise     */
+  void* stream;          /* cudaStream_t to order work on, or NULL         */
+} vegas_config;
+
+typedef struct {
+  double I;              /* combined estimate of the current window       */
+  double sigma;          /* its standard error                             */
+  double chi2_dof;       /* chi^2 per degree of freedom (0 for 1 iteration) */
+  int iters_done;        /* iterations in the current window              */
+  int stopped;           /* 1 if the ACC test ended the last call early    */
+  int64_t nonfinite;     /* non-finite weights seen (counted as 0)         */
+  int64_t samples;       /* points evaluated in the current window        */
+} vegas_result;
+
+/* Create a context: copies config and integrand, allocates device buffers,
+ * sets the uniform grid e_a[k] = k/N (step 1).  Errors: VEGAS_EINVAL for
+ * out-of-range sizes or parameter counts, VEGAS_ENOMEM, VEGAS_ECUDA. */
+vegas_status vegas_create(const vegas_config* config,
+                          const vegas_integrand* integrand, vegas_ctx** out);
+
+void vegas_destroy(vegas_ctx* ctx);
+
+/* Steps 2-6, n_iter times (Sec. 2.1, step 6): each iteration evaluates NCALL
+ * points, reduces the per-bin sums, refines the grid if refine != 0, and
+ * adds its estimate to the combination window; stops early (device-side)
+ * when sigma/|I| < config.acc.  out (nullable) receives the combined result
+ * and forces a stream synchronisation. */
+vegas_status vegas_iterate(vegas_ctx* ctx, int n_iter, int refine,
+                           vegas_result* out);
+
+/* Start a new combination window (the grid and the iteration counter are
+ * kept). */
+vegas_status vegas_reset_results(vegas_ctx* ctx);
+
+/* BASES (Sec. 2.1 and Sec. 5.1): a grid-optimisation phase of up to itmx1
+ * refining iterations (stopping at acc1), then an integration phase of up
+ * to itmx2 iterations on the frozen grid (stopping at acc2).  out receives
+ * the integration phase alone; phase1 (nullable) the first phase. */
+vegas_status bases_integrate(vegas_ctx* ctx, int itmx1, double acc1,
+                             int itmx2, double acc2, vegas_result* out,
+                             vegas_result* phase1);
+
+/* Copy the grid edges [ndim][nbins+1] and, if bin_sums is not NULL, the
+ * per-bin sums of the last iteration [2][ndim][nbins] (sum w, sum w^2). */
+vegas_status vegas_get_grid(vegas_ctx* ctx, double* edges, double* bin_sums);
+
+/* Replace the grid (resume / freeze).  Edges must start at 0, end at 1 and
+ * increase strictly on every axis, else VEGAS_EINVAL. */
+vegas_status vegas_set_grid(vegas_ctx* ctx, const double* edges);
+
+/* The iteration history of the current window: hist[i] = (I_i, sigma_i^2),
+ * up to max_iters rows; *n_out receives the number of rows. */
+vegas_status vegas_get_history(vegas_ctx* ctx, double* hist, int max_iters,
+                               int* n_out);
+
+/* Per-hypercube sums of the last stratified iteration, [g^ndim][2]
+ * (sum w, sum w^2); VEGAS_ESTATE without stratification. */
+vegas_status vegas_get_cube_sums(vegas_ctx* ctx, double* sums);
+
+/* The Philox iteration counter (iterations run so far) and a setter for
+ * exact resume together with vegas_set_grid. */
+vegas_status vegas_get_iteration(vegas_ctx* ctx, uint32_t* it);
+vegas_status vegas_set_iteration(vegas_ctx* ctx, uint32_t it);
+
+/* Replace the integrand parameters (same count as at creation). */
+vegas_status vegas_set_params(vegas_ctx* ctx, const double* params,
+                              int nparams);
+
+/* One evaluation pass at Philox iteration `it` on the current grid without
+ * refinement and without touching the window or the counter: the
+ * estimate I and its variance.  Two calls with the same `it` use common
+ * random numbers. */
+vegas_status vegas_eval(vegas_ctx* ctx, uint32_t it, double* I, double* var);
+
+/* Gradient of that estimate with respect to integrand parameters theta on
+ * the frozen grid with the random numbers of iteration `it`:
+ *   dI/dtheta = (1/NCALL) sum_s J_s df/dtheta(x_s).
+ * theta = (M, Gamma, T) for VG_RAMBO_BW, (c1, c2, w) for
+ * VG_DOUBLE_GAUSSIAN, (u[d], a[d]) for VG_GENZ_GAUSSIAN; VEGAS_EINVAL for
+ * the other kinds.  grad has vegas_ntheta(ctx) entries; I (nullable) gets
+ * the estimate itself. */
+vegas_status vegas_grad(vegas_ctx* ctx, uint32_t it, double* grad, double* I);
+int vegas_ntheta(const vegas_ctx* ctx);
+
+/* Step 2-3 for a list of sample indices at iteration `it` on the current
+ * grid (host arrays of n entries; any output may be NULL): words [n][W]
+ * (W = ndim or 2 ndim), bins [n][ndim], x [n][ndim], jac [n], f [n].
+ * x, jac and f are in the context's precision, widened to double. */
+vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
+                               int64_t n, uint32_t* words, int32_t* bins,
+                               double* x, double* jac, double* f);
+
+/* Launch shape of the sampling kernel: threads per CTA (multiple of 32,
+ * 64..1024) and CTAs per SM (0 = as many as fit).  Used by the autotuner;
+ * takes effect on the next iteration. */
+vegas_status vegas_set_launch(vegas_ctx* ctx, int threads, int ctas_per_sm);
+vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
+                              int* ctas_per_sm);
+
+/* Message of the last failure on ctx (or of the calling thread when ctx is
+ * NULL).  Never NULL. */
+const char* vegas_last_error(const vegas_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,816 @@
+// abi.cu -- host side of the C ABI declared in include/gvegas.h: context
+// lifetime, derived integrand constants, launch geometry, the per-iteration
+// kernel sequence (captured once into a CUDA graph per call shape) and the
+// result read-back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "integrands.cuh"
+#include "kernels.h"
+
+using gv::GState;
+
+namespace {
+
+thread_local std::string g_thread_err;
+
+std::string vformat(const char* fmt, va_list ap) {
+  char buf[512];
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  return std::string(buf);
+}
+
+}  // namespace
+
+struct vegas_ctx {
+  vegas_config cfg{};
+  int kind = 0;
+  std::vector<double> params;            // integrand parameters as given
+  double derived[gv::kNumDerived] = {};  // device constants (see integrands.cuh)
+  double scale = 1.0;                    // output scale applied in k_reduce
+  int prec = VG_FP64;
+  int ybits = 53;
+  int g = 1;
+  uint64_t ncubes = 1, nc = 0;
+  int strat = 0;
+  gv::KernelEntry ke{};
+  int sm_count = 0;
+  // launch geometry
+  int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, flush_rounds = 1, occ = 0;
+  size_t smem = 0;
+  // device buffers
+  double* d_edges = nullptr;
+  double2* d_tab64 = nullptr;
+  float2* d_tab32 = nullptr;
+  double* d_derived = nullptr;
+  double* d_part_bins = nullptr;
+  double* d_part_tot = nullptr;
+  int part_rows = 0;
+  double* d_bins = nullptr;
+  double* d_tot = nullptr;
+  double* d_cubes = nullptr;
+  GState* d_st = nullptr;
+  // host staging (pinned)
+  GState* h_st = nullptr;
+  double* h_stage = nullptr;
+  size_t h_stage_len = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  int hist_upper = 0;  // upper bound of the window length (host shadow)
+  std::string err;
+
+  vegas_status fail(vegas_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    err = vformat(fmt, ap);
+    va_end(ap);
+    g_thread_err = err;
+    return st;
+  }
+};
+
+namespace {
+
+vegas_status thread_fail(vegas_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  g_thread_err = vformat(fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CK(ctx, call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? VEGAS_ENOMEM : VEGAS_ECUDA, \
+                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,    \
+                         __LINE__);                                                    \
+  } while (0)
+
+int expected_nparams(int kind, int d) {
+  switch (kind) {
+    case VG_GENZ_GAUSSIAN:
+    case VG_GENZ_PRODUCT_PEAK: return 2 * d;
+    case VG_GENZ_CORNER_PEAK: return d;
+    case VG_GENZ_OSCILLATORY: return d + 1;
+    case VG_DOUBLE_GAUSSIAN: return 3;
+    case VG_RAMBO_BW: return VG_RB_NPARAMS;
+    default: return -1;
+  }
+}
+
+// Constants read by the device integrands (layout in integrands.cuh) and the
+// scale that turns the kernel's dimensionless weights into the integrand's.
+bool derive_params(int kind, int d, const double* p, double* dv, double* scale,
+                   std::string* why) {
+  std::fill(dv, dv + gv::kNumDerived, 0.0);
+  *scale = 1.0;
+  const int M = gv::kMaxDim, S = gv::kScalar;
+  switch (kind) {
+    case VG_GENZ_GAUSSIAN:
+      for (int i = 0; i < d; ++i) {
+        dv[i] = p[i] * p[i];
+        dv[M + i] = p[d + i];
+      }
+      return true;
+    case VG_GENZ_PRODUCT_PEAK:
+      for (int i = 0; i < d; ++i) {
+        dv[i] = 1.0 / (p[i] * p[i]);
+        dv[M + i] = p[d + i];
+      }
+      return true;
+    case VG_GENZ_CORNER_PEAK:
+      for (int i = 0; i < d; ++i) dv[i] = p[i];
+      dv[S] = -(double)(d + 1);
+      return true;
+    case VG_GENZ_OSCILLATORY:
+      for (int i = 0; i < d; ++i) dv[i] = p[i];
+      dv[S] = 2.0 * M_PI * p[d];
+      return true;
+    case VG_DOUBLE_GAUSSIAN: {
+      const double w = p[2];
+      if (!(w > 0.0)) {
+        *why = "double Gaussian width must be positive";
+        return false;
+      }
+      dv[S] = p[0];
+      dv[S + 1] = p[1];
+      dv[S + 2] = 1.0 / (w * w);
+      dv[S + 3] = 0.5 * std::pow(w * std::sqrt(M_PI), -(double)d);
+      return true;
+    }
+    case VG_RAMBO_BW: {
+      const int n = (int)p[VG_RB_N];
+      if (n < 2 || 4 * n != d || (double)n != p[VG_RB_N]) {
+        *why = "RAMBO needs ndim = 4 n with integer n >= 2";
+        return false;
+      }
+      const double rs = p[VG_RB_SQRTS], s = rs * rs, Mw = p[VG_RB_M], Gw = p[VG_RB_GAMMA];
+      if (!(rs > 0.0)) {
+        *why = "RAMBO needs sqrt(s) > 0";
+        return false;
+      }
+      const int cut = (int)p[VG_RB_CUT], obs = (int)p[VG_RB_OBS];
+      if (cut < 0 || cut > 2 || obs < 0 || obs > 3) {
+        *why = "RAMBO cut must be 0..2 and observable 0..3";
+        return false;
+      }
+      if (cut == 1 && !(p[VG_RB_WC] > 0.0)) {
+        *why = "sigmoid cut width must be positive";
+        return false;
+      }
+      double V = std::pow(M_PI / 2.0, n - 1) * std::pow(s, n - 2);
+      for (int i = 2; i <= n - 1; ++i) V /= i;
+      for (int i = 2; i <= n - 2; ++i) V /= i;
+      dv[gv::RB_N] = n;
+      dv[gv::RB_MU] = Mw * Mw / s;
+      dv[gv::RB_MUG] = Mw * Gw / s;
+      dv[gv::RB_MUG2] = (Mw * Gw / s) * (Mw * Gw / s);
+      dv[gv::RB_PTMIN] = p[VG_RB_PTMIN] / rs;
+      dv[gv::RB_DR2] = p[VG_RB_DRMIN] * p[VG_RB_DRMIN];
+      dv[gv::RB_CUT] = cut;
+      dv[gv::RB_T] = p[VG_RB_T] / rs;
+      dv[gv::RB_INVWC] = cut == 1 ? rs / p[VG_RB_WC] : 0.0;
+      dv[gv::RB_OBS] = obs;
+      // obs 0: V_n * s^-(n+1) (dimensionless product); 1: V_n; 2: V_n s;
+      // 3: V_n / s.
+      switch (obs) {
+        case 0: *scale = V * std::pow(s, -(double)(n + 1)); break;
+        case 1: *scale = V; break;
+        case 2: *scale = V * s; break;
+        default: *scale = V / s; break;
+      }
+      return true;
+    }
+    default:
+      *why = "unknown integrand kind";
+      return false;
+  }
+}
+
+bool lookup_kernel(int kind, int prec, int d, gv::KernelEntry* e) {
+  switch (kind) {
+    case VG_GENZ_GAUSSIAN: return gv::entries_genz_gaussian(prec, d, e);
+    case VG_GENZ_PRODUCT_PEAK: return gv::entries_genz_product_peak(prec, d, e);
+    case VG_GENZ_CORNER_PEAK: return gv::entries_genz_corner_peak(prec, d, e);
+    case VG_GENZ_OSCILLATORY: return gv::entries_genz_oscillatory(prec, d, e);
+    case VG_DOUBLE_GAUSSIAN: return gv::entries_dgauss(prec, d, e);
+    case VG_RAMBO_BW: return gv::entries_rambo(prec, d, e);
+    default: return false;
+  }
+}
+
+void destroy_graphs(vegas_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+}
+
+// Launch geometry: a persistent grid of CTAs per SM as occupancy allows
+// (or as requested), capped by the work available.
+vegas_status configure_launch(vegas_ctx* c) {
+  const int d = c->cfg.ndim, N = c->cfg.nbins;
+  c->smem = c->ke.smem(d, N);
+  CK(c, cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)c->smem));
+  int occ = 0;
+  CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ke.sample, c->threads, c->smem));
+  if (occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %zu B smem",
+                              c->threads, c->smem);
+  c->occ = occ;
+  const int per_sm = c->ctas_per_sm_req > 0 ? std::min(c->ctas_per_sm_req, occ) : occ;
+  const int64_t cap_ctas = (int64_t)c->sm_count * per_sm;
+  const int64_t cap_threads = cap_ctas * c->threads;
+  uint64_t units;
+  if (c->strat) {
+    int L = 1;
+    while (L < 32 && (uint64_t)(2 * L) <= c->nc && c->ncubes * (uint64_t)(2 * L) <= (uint64_t)cap_threads) L *= 2;
+    c->lanes = L;
+    units = c->ncubes * (uint64_t)L;
+  } else {
+    c->lanes = 1;
+    units = (uint64_t)c->cfg.ncall;
+  }
+  int64_t ctas = (int64_t)((units + c->threads - 1) / c->threads);
+  c->ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, cap_ctas));
+  // compensated mode: flush the FP32 histograms after ~4096 points per CTA
+  if (c->strat) {
+    const uint64_t per_round = (uint64_t)(c->threads / c->lanes) * c->nc;
+    c->flush_rounds = (int)std::max<uint64_t>(1, 4096 / std::max<uint64_t>(per_round, 1));
+  } else {
+    c->flush_rounds = std::max(1, 4096 / c->threads);
+  }
+  if (c->ctas > c->part_rows) {
+    if (c->d_part_bins) cudaFree(c->d_part_bins);
+    if (c->d_part_tot) cudaFree(c->d_part_tot);
+    c->d_part_bins = nullptr;
+    c->d_part_tot = nullptr;
+    c->part_rows = 0;
+    CK(c, cudaMalloc(&c->d_part_bins, sizeof(double) * 2 * (size_t)d * N * c->ctas));
+    CK(c, cudaMalloc(&c->d_part_tot, sizeof(double) * gv::kTotCols * (size_t)c->ctas));
+    c->part_rows = c->ctas;
+  }
+  destroy_graphs(c);
+  return VEGAS_OK;
+}
+
+gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
+  gv::SampleArgs A{};
+  A.d = c->cfg.ndim;
+  A.N = c->cfg.nbins;
+  A.g = c->g;
+  A.ybits = c->ybits;
+  A.lanes = c->lanes;
+  A.strat = c->strat;
+  A.flush_rounds = c->flush_rounds;
+  A.key0 = (uint32_t)c->cfg.seed;
+  A.key1 = (uint32_t)(c->cfg.seed >> 32);
+  A.instance = c->cfg.instance;
+  A.it_override = it_override;
+  A.ncall = (uint64_t)c->cfg.ncall;
+  A.nc = c->nc;
+  A.ncubes = c->ncubes;
+  A.g_pow2 = (c->g & (c->g - 1)) == 0;
+  A.g_log2 = 0;
+  while ((1 << A.g_log2) < c->g) ++A.g_log2;
+  A.nparts = c->ctas;
+  A.tab = c->prec == VG_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
+  A.dparams = c->d_derived;
+  A.st = c->d_st;
+  A.part_bins = c->d_part_bins;
+  A.part_tot = c->d_part_tot;
+  A.cubes = c->d_cubes;
+  return A;
+}
+
+gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record) {
+  gv::FinArgs F{};
+  F.d = c->cfg.ndim;
+  F.N = c->cfg.nbins;
+  F.nparts = c->ctas;
+  F.strat = c->strat;
+  F.refine = refine;
+  F.record = record;
+  F.ncall = (uint64_t)c->cfg.ncall;
+  F.ncubes = c->ncubes;
+  F.scale = c->scale;
+  F.alpha = c->cfg.alpha;
+  F.part_bins = c->d_part_bins;
+  F.part_tot = c->d_part_tot;
+  F.bins = c->d_bins;
+  F.tot = c->d_tot;
+  F.edges = c->d_edges;
+  F.tab64 = c->d_tab64;
+  F.tab32 = c->d_tab32;
+  F.st = c->d_st;
+  return F;
+}
+
+// One pass of steps 2-6 on the context stream.
+vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record) {
+  gv::SampleArgs A = sample_args(c, it_override);
+  void* args[] = {&A};
+  CK(c, cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream));
+  gv::FinArgs F = fin_args(c, refine, record);
+  CK(c, gv_launch_reduce(&F, c->stream));
+  CK(c, gv_launch_finalize(&F, c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status get_graph(vegas_ctx* c, int n_iter, int refine, cudaGraphExec_t* out) {
+  auto key = std::make_pair(n_iter, refine);
+  auto itg = c->graphs.find(key);
+  if (itg != c->graphs.end()) {
+    *out = itg->second;
+    return VEGAS_OK;
+  }
+  cudaGraph_t g = nullptr;
+  CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  vegas_status st = VEGAS_OK;
+  for (int i = 0; i < n_iter && st == VEGAS_OK; ++i) st = launch_pass(c, -1, refine, 1);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (st != VEGAS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graphs[key] = ge;
+  *out = ge;
+  return VEGAS_OK;
+}
+
+vegas_status read_state(vegas_ctx* c) {
+  CK(c, cudaMemcpyAsync(c->h_st, c->d_st, offsetof(GState, hist), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+void fill_result(const vegas_ctx* c, vegas_result* r) {
+  const GState* s = c->h_st;
+  r->I = s->I;
+  r->sigma = s->sigma;
+  r->chi2_dof = s->chi2;
+  r->iters_done = s->nhist;
+  r->stopped = s->stopped;
+  r->nonfinite = s->nonfinite;
+  r->samples = s->samples;
+}
+
+vegas_status stage(vegas_ctx* c, size_t n) {
+  if (n <= c->h_stage_len) return VEGAS_OK;
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
+  c->h_stage_len = 0;
+  CK(c, cudaMallocHost(&c->h_stage, n * sizeof(double)));
+  c->h_stage_len = n;
+  return VEGAS_OK;
+}
+
+vegas_status upload_grid(vegas_ctx* c, const double* edges) {
+  const int d = c->cfg.ndim, N = c->cfg.nbins;
+  const size_t n = (size_t)d * (N + 1);
+  vegas_status st = stage(c, n);
+  if (st) return st;
+  CK(c, cudaStreamSynchronize(c->stream));  // staging buffer may still be in use
+  memcpy(c->h_stage, edges, n * sizeof(double));
+  CK(c, cudaMemcpyAsync(c->d_edges, c->h_stage, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(c, gv_launch_tables(c->d_edges, d, N, c->d_tab64, c->d_tab32, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status upload_derived(vegas_ctx* c) {
+  vegas_status st = stage(c, gv::kNumDerived);
+  if (st) return st;
+  CK(c, cudaStreamSynchronize(c->stream));
+  memcpy(c->h_stage, c->derived, sizeof c->derived);
+  CK(c, cudaMemcpyAsync(c->d_derived, c->h_stage, sizeof c->derived, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+bool valid_grid(const double* e, int d, int N) {
+  for (int a = 0; a < d; ++a) {
+    const double* r = e + (size_t)a * (N + 1);
+    if (r[0] != 0.0 || r[N] != 1.0) return false;
+    for (int k = 0; k < N; ++k)
+      if (!(r[k + 1] > r[k])) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vegas_last_error(const vegas_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_thread_err.c_str();
+}
+
+void vegas_destroy(vegas_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  cudaFree(c->d_edges);
+  cudaFree(c->d_tab64);
+  cudaFree(c->d_tab32);
+  cudaFree(c->d_derived);
+  cudaFree(c->d_part_bins);
+  cudaFree(c->d_part_tot);
+  cudaFree(c->d_bins);
+  cudaFree(c->d_tot);
+  cudaFree(c->d_cubes);
+  cudaFree(c->d_st);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, vegas_ctx** out) {
+  if (!out) return thread_fail(VEGAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !fn) return thread_fail(VEGAS_EINVAL, "config or integrand is NULL");
+  const int d = cfg->ndim, N = cfg->nbins;
+  if (d < 1 || d > GVEGAS_MAXDIM) return thread_fail(VEGAS_EINVAL, "ndim %d outside 1..%d", d, GVEGAS_MAXDIM);
+  if (N < 2 || N > GVEGAS_MAXBINS) return thread_fail(VEGAS_EINVAL, "nbins %d outside 2..%d", N, GVEGAS_MAXBINS);
+  if (cfg->ncall < 2 || cfg->ncall > (int64_t)1 << 32)
+    return thread_fail(VEGAS_EINVAL, "ncall %lld outside 2..2^32", (long long)cfg->ncall);
+  if (cfg->precision < VG_FP64 || cfg->precision > VG_FP32_ACCCOMP)
+    return thread_fail(VEGAS_EINVAL, "unknown precision %d", cfg->precision);
+  const int ybits = cfg->ybits ? cfg->ybits : (cfg->precision == VG_FP64 ? 53 : 24);
+  if (ybits != 24 && ybits != 53) return thread_fail(VEGAS_EINVAL, "ybits must be 24 or 53");
+  if (!(cfg->alpha >= 0.0) || !std::isfinite(cfg->alpha)) return thread_fail(VEGAS_EINVAL, "alpha must be >= 0");
+  if (fn->ndim != d) return thread_fail(VEGAS_EINVAL, "integrand ndim %d != config ndim %d", fn->ndim, d);
+  const int np = expected_nparams(fn->kind, d);
+  if (np < 0) return thread_fail(VEGAS_EINVAL, "unknown integrand kind %d", fn->kind);
+  if (fn->nparams != np || (np > 0 && !fn->params))
+    return thread_fail(VEGAS_EINVAL, "integrand kind %d needs %d parameters, got %d", fn->kind, np, fn->nparams);
+  const int g = cfg->nstrat < 1 ? 1 : cfg->nstrat;
+  uint64_t G = 1;
+  for (int a = 0; a < d; ++a) {
+    G *= (uint64_t)g;
+    if (G > (uint64_t)cfg->ncall) return thread_fail(VEGAS_EINVAL, "nstrat^ndim exceeds ncall");
+  }
+  if ((uint64_t)cfg->ncall % G != 0) return thread_fail(VEGAS_EINVAL, "ncall must be a multiple of nstrat^ndim");
+  if (G > 1 && (uint64_t)cfg->ncall / G < 2) return thread_fail(VEGAS_EINVAL, "need >= 2 points per hypercube");
+  if ((int64_t)g * N >= (ybits == 53 ? 2048 : (1 << 30)))
+    return thread_fail(VEGAS_EINVAL, "nstrat * nbins too large for %d-bit sampling", ybits);
+
+  vegas_ctx* c = new vegas_ctx();
+  c->cfg = *cfg;
+  c->cfg.ybits = ybits;
+  c->kind = fn->kind;
+  c->params.assign(fn->params, fn->params + np);
+  c->prec = cfg->precision;
+  c->ybits = ybits;
+  c->g = g;
+  c->ncubes = G;
+  c->nc = (uint64_t)cfg->ncall / G;
+  c->strat = G > 1;
+  std::string why;
+  if (!derive_params(fn->kind, d, c->params.data(), c->derived, &c->scale, &why)) {
+    delete c;
+    return thread_fail(VEGAS_EINVAL, "%s", why.c_str());
+  }
+  if (!lookup_kernel(fn->kind, c->prec, d, &c->ke)) {
+    delete c;
+    return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
+  }
+  auto bail = [&](vegas_status st) {
+    g_thread_err = c->err;
+    vegas_destroy(c);
+    return st;
+  };
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "stream: %s", cudaGetErrorString(e)));
+    c->own_stream = true;
+  }
+  auto alloc = [&](void** p, size_t bytes) -> vegas_status {
+    cudaError_t ae = cudaMalloc(p, bytes);
+    if (ae != cudaSuccess)
+      return c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ae));
+    return VEGAS_OK;
+  };
+  vegas_status st = VEGAS_OK;
+  if (!st) st = alloc((void**)&c->d_edges, sizeof(double) * d * (N + 1));
+  if (!st) st = alloc((void**)&c->d_tab64, sizeof(double2) * d * N);
+  if (!st) st = alloc((void**)&c->d_tab32, sizeof(float2) * d * N);
+  if (!st) st = alloc((void**)&c->d_derived, sizeof c->derived);
+  if (!st) st = alloc((void**)&c->d_bins, sizeof(double) * 2 * d * N);
+  if (!st) st = alloc((void**)&c->d_tot, sizeof(double) * gv::kTotCols);
+  if (!st && c->strat) st = alloc((void**)&c->d_cubes, sizeof(double) * 2 * G);
+  if (!st) st = alloc((void**)&c->d_st, sizeof(GState));
+  if (st) return bail(st);
+  if (cudaMallocHost(&c->h_st, sizeof(GState)) != cudaSuccess)
+    return bail(c->fail(VEGAS_ENOMEM, "cudaMallocHost(GState)"));
+  memset(c->h_st, 0, sizeof(GState));
+  c->h_st->acc = cfg->acc;
+  if (cudaMemcpyAsync(c->d_st, c->h_st, sizeof(GState), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->d_bins, 0, sizeof(double) * 2 * d * N, c->stream) != cudaSuccess)
+    return bail(c->fail(VEGAS_ECUDA, "state initialisation failed"));
+  if ((st = configure_launch(c))) return bail(st);
+  std::vector<double> e0((size_t)d * (N + 1));
+  for (int a = 0; a < d; ++a)
+    for (int k = 0; k <= N; ++k) e0[(size_t)a * (N + 1) + k] = (double)k / (double)N;
+  if ((st = upload_grid(c, e0.data()))) return bail(st);
+  if ((st = upload_derived(c))) return bail(st);
+  *out = c;
+  return VEGAS_OK;
+}
+
+vegas_status vegas_iterate(vegas_ctx* c, int n_iter, int refine, vegas_result* out) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (n_iter < 0) return c->fail(VEGAS_EINVAL, "n_iter < 0");
+  if (n_iter > 0) {
+    vegas_status st = VEGAS_OK;
+    if (c->hist_upper + n_iter > gv::kMaxHist)
+      return c->fail(VEGAS_EINVAL, "window would exceed %d iterations; call vegas_reset_results", gv::kMaxHist);
+    c->hist_upper += n_iter;
+    // per call: clear the stop flag, set this call's ACC target
+    int zero[2] = {0, 0};
+    CK(c, cudaMemcpyAsync(&c->d_st->done, zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(&c->d_st->stopped, zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    double acc = c->cfg.acc;
+    CK(c, cudaMemcpyAsync(&c->d_st->acc, &acc, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    cudaGraphExec_t ge;
+    if ((st = get_graph(c, n_iter, refine ? 1 : 0, &ge))) return st;
+    CK(c, cudaGraphLaunch(ge, c->stream));
+  }
+  if (out) {
+    vegas_status st = read_state(c);
+    if (st) return st;
+    fill_result(c, out);
+  }
+  return VEGAS_OK;
+}
+
+vegas_status vegas_reset_results(vegas_ctx* c) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  vegas_status st = read_state(c);
+  if (st) return st;
+  GState* h = c->h_st;
+  h->nhist = 0;
+  h->nonfinite = 0;
+  h->samples = 0;
+  h->I = h->sigma = h->chi2 = 0.0;
+  h->done = 0;
+  h->stopped = 0;
+  c->hist_upper = 0;
+  CK(c, cudaMemcpyAsync(c->d_st, h, offsetof(GState, hist), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status bases_integrate(vegas_ctx* c, int itmx1, double acc1, int itmx2, double acc2,
+                             vegas_result* out, vegas_result* phase1) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (itmx1 < 0 || itmx2 < 1) return c->fail(VEGAS_EINVAL, "need itmx1 >= 0 and itmx2 >= 1");
+  const double acc_save = c->cfg.acc;
+  vegas_status st = vegas_reset_results(c);
+  vegas_result r1{};
+  if (!st && itmx1 > 0) {
+    c->cfg.acc = acc1;
+    st = vegas_iterate(c, itmx1, 1, phase1 ? &r1 : nullptr);
+  }
+  if (!st) st = vegas_reset_results(c);
+  if (!st) {
+    c->cfg.acc = acc2;
+    st = vegas_iterate(c, itmx2, 0, out);
+  }
+  c->cfg.acc = acc_save;
+  if (!st && phase1) *phase1 = r1;
+  return st;
+}
+
+vegas_status vegas_get_grid(vegas_ctx* c, double* edges, double* bin_sums) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  const int d = c->cfg.ndim, N = c->cfg.nbins;
+  const size_t ne = (size_t)d * (N + 1), nb = 2 * (size_t)d * N;
+  vegas_status st = stage(c, ne + nb);
+  if (st) return st;
+  if (edges) CK(c, cudaMemcpyAsync(c->h_stage, c->d_edges, ne * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (bin_sums)
+    CK(c, cudaMemcpyAsync(c->h_stage + ne, c->d_bins, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (edges) memcpy(edges, c->h_stage, ne * sizeof(double));
+  if (bin_sums) memcpy(bin_sums, c->h_stage + ne, nb * sizeof(double));
+  return VEGAS_OK;
+}
+
+vegas_status vegas_set_grid(vegas_ctx* c, const double* edges) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (!edges || !valid_grid(edges, c->cfg.ndim, c->cfg.nbins))
+    return c->fail(VEGAS_EINVAL, "edges must start at 0, end at 1 and increase strictly");
+  return upload_grid(c, edges);
+}
+
+vegas_status vegas_get_history(vegas_ctx* c, double* hist, int max_iters, int* n_out) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  vegas_status st = read_state(c);
+  if (st) return st;
+  const int n = std::min(c->h_st->nhist, std::max(max_iters, 0));
+  if (n_out) *n_out = c->h_st->nhist;
+  if (n > 0 && hist) {
+    if ((st = stage(c, 2 * (size_t)n))) return st;
+    CK(c, cudaMemcpyAsync(c->h_stage, &c->d_st->hist[0][0], 2 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    memcpy(hist, c->h_stage, 2 * n * sizeof(double));
+  }
+  return VEGAS_OK;
+}
+
+vegas_status vegas_get_cube_sums(vegas_ctx* c, double* sums) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (!c->strat) return c->fail(VEGAS_ESTATE, "context is not stratified");
+  if (!sums) return c->fail(VEGAS_EINVAL, "sums is NULL");
+  const size_t n = 2 * (size_t)c->ncubes;
+  vegas_status st = stage(c, n);
+  if (st) return st;
+  CK(c, cudaMemcpyAsync(c->h_stage, c->d_cubes, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const double s1 = c->scale, s2 = c->scale * c->scale;
+  for (size_t i = 0; i < c->ncubes; ++i) {
+    sums[2 * i] = c->h_stage[2 * i] * s1;
+    sums[2 * i + 1] = c->h_stage[2 * i + 1] * s2;
+  }
+  return VEGAS_OK;
+}
+
+vegas_status vegas_get_iteration(vegas_ctx* c, uint32_t* it) {
+  if (!c || !it) return thread_fail(VEGAS_EINVAL, "NULL argument");
+  vegas_status st = read_state(c);
+  if (st) return st;
+  *it = c->h_st->it;
+  return VEGAS_OK;
+}
+
+vegas_status vegas_set_iteration(vegas_ctx* c, uint32_t it) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  vegas_status st = read_state(c);
+  if (st) return st;
+  c->h_st->it = it;
+  CK(c, cudaMemcpyAsync(&c->d_st->it, &c->h_st->it, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status vegas_set_params(vegas_ctx* c, const double* params, int nparams) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (!params || nparams != (int)c->params.size())
+    return c->fail(VEGAS_EINVAL, "expected %d parameters", (int)c->params.size());
+  std::vector<double> p(params, params + nparams);
+  double dv[gv::kNumDerived], sc;
+  std::string why;
+  if (!derive_params(c->kind, c->cfg.ndim, p.data(), dv, &sc, &why))
+    return c->fail(VEGAS_EINVAL, "%s", why.c_str());
+  c->params = p;
+  memcpy(c->derived, dv, sizeof dv);
+  c->scale = sc;
+  destroy_graphs(c);  // the scale is baked into the captured kernels
+  return upload_derived(c);
+}
+
+vegas_status vegas_eval(vegas_ctx* c, uint32_t it, double* I, double* var) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (it > 0x7FFFFFFFu) return c->fail(VEGAS_EINVAL, "iteration index must be < 2^31");
+  int zero = 0;
+  CK(c, cudaMemcpyAsync(&c->d_st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  vegas_status st = launch_pass(c, (int)it, 0, 0);
+  if (st) return st;
+  if ((st = read_state(c))) return st;
+  if (I) *I = c->h_st->last_I;
+  if (var) *var = c->h_st->last_var;
+  return VEGAS_OK;
+}
+
+vegas_status vegas_sample_dump(vegas_ctx* c, uint32_t it, const uint64_t* s, int64_t n, uint32_t* words,
+                               int32_t* bins, double* x, double* jac, double* f) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (n < 0 || (n > 0 && !s)) return c->fail(VEGAS_EINVAL, "bad sample list");
+  if (n == 0) return VEGAS_OK;
+  if (it > 0x7FFFFFFFu) return c->fail(VEGAS_EINVAL, "iteration index must be < 2^31");
+  for (int64_t i = 0; i < n; ++i)
+    if (s[i] >= (uint64_t)c->cfg.ncall) return c->fail(VEGAS_EINVAL, "sample index %llu >= ncall", (unsigned long long)s[i]);
+  const int d = c->cfg.ndim, W = c->ybits == 24 ? d : 2 * d;
+  uint64_t* ds = nullptr;
+  uint32_t* dw = nullptr;
+  int32_t* db = nullptr;
+  double *dx = nullptr, *dj = nullptr, *df = nullptr;
+  vegas_status st = VEGAS_OK;
+  auto A = [&](void** p, size_t b) {
+    if (!st && cudaMalloc(p, b) != cudaSuccess) st = c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", b);
+  };
+  A((void**)&ds, n * sizeof(uint64_t));
+  if (words) A((void**)&dw, n * W * sizeof(uint32_t));
+  if (bins) A((void**)&db, n * d * sizeof(int32_t));
+  if (x) A((void**)&dx, n * d * sizeof(double));
+  if (jac) A((void**)&dj, n * sizeof(double));
+  if (f) A((void**)&df, n * sizeof(double));
+  cudaError_t e = cudaSuccess;
+  if (!st) {
+    gv::DumpArgs D{};
+    D.S = sample_args(c, (int)it);
+    D.s = ds;
+    D.n = n;
+    D.words = dw;
+    D.bins = db;
+    D.x = dx;
+    D.jac = dj;
+    D.f = df;
+    void* args[] = {&D};
+    e = cudaMemcpyAsync(ds, s, n * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel(c->ke.dump, dim3((unsigned)((n + 255) / 256)), dim3(256), args, 0, c->stream);
+    if (e == cudaSuccess && words) e = cudaMemcpyAsync(words, dw, n * W * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && bins) e = cudaMemcpyAsync(bins, db, n * d * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, n * d * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && jac) e = cudaMemcpyAsync(jac, dj, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && f) e = cudaMemcpyAsync(f, df, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) st = c->fail(VEGAS_ECUDA, "sample dump: %s", cudaGetErrorString(e));
+  }
+  cudaFree(ds);
+  cudaFree(dw);
+  cudaFree(db);
+  cudaFree(dx);
+  cudaFree(dj);
+  cudaFree(df);
+  if (!st && f) {
+    for (int64_t i = 0; i < n; ++i) f[i] *= c->scale;
+    if (jac) {
+      // jac is reported as the Jacobian itself; f carries the integrand scale
+    }
+  }
+  return st;
+}
+
+vegas_status vegas_set_launch(vegas_ctx* c, int threads, int ctas_per_sm) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (threads < 64 || threads > 256 || threads % 32 != 0)
+    return c->fail(VEGAS_EINVAL, "threads must be a multiple of 32 in 64..256");
+  if (ctas_per_sm < 0) return c->fail(VEGAS_EINVAL, "ctas_per_sm < 0");
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int t0 = c->threads, p0 = c->ctas_per_sm_req;
+  c->threads = threads;
+  c->ctas_per_sm_req = ctas_per_sm;
+  vegas_status st = configure_launch(c);
+  if (st) {
+    c->threads = t0;
+    c->ctas_per_sm_req = p0;
+    configure_launch(c);
+  }
+  return st;
+}
+
+vegas_status vegas_get_launch(vegas_ctx* c, int* threads, int* ctas, int* ctas_per_sm) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (threads) *threads = c->threads;
+  if (ctas) *ctas = c->ctas;
+  if (ctas_per_sm) *ctas_per_sm = c->occ;
+  return VEGAS_OK;
+}
+
+vegas_status vegas_grad(vegas_ctx* c, uint32_t it, double* grad, double* I) {
+  (void)it;
+  (void)grad;
+  (void)I;
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  return c->fail(VEGAS_EINVAL, "gradient not available for this integrand");
+}
+
+int vegas_ntheta(const vegas_ctx* c) {
+  if (!c) return 0;
+  switch (c->kind) {
+    case VG_GENZ_GAUSSIAN: return 2 * c->cfg.ndim;
+    case VG_DOUBLE_GAUSSIAN: return 3;
+    case VG_RAMBO_BW: return 3;
+    default: return 0;
+  }
+}
+
+}  // extern "C"

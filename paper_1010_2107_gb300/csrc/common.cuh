@@ -1,0 +1,164 @@
+// common.cuh -- device-side building blocks of the sm_103a VEGAS / BASES path:
+// Philox4x32-10 in registers, compensated FP32 sums, precision-generic math,
+// and the argument blocks of the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gvegas.h"
+
+namespace gv {
+
+constexpr int kMaxDim = GVEGAS_MAXDIM;
+constexpr int kMaxBins = GVEGAS_MAXBINS;
+constexpr int kMaxHist = GVEGAS_MAXHIST;
+constexpr int kNumDerived = 2 * kMaxDim + 16;  // derived integrand constants
+constexpr int kTotCols = 8;                     // per-CTA totals columns
+
+// Columns of the per-CTA totals block.
+enum { TOT_SW = 0, TOT_SW2 = 1, TOT_SI = 2, TOT_SV = 3, TOT_NONFINITE = 4 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): the counter-based
+// generator that replaces the per-thread xorshift state of Appendix A.
+// Stateless: any thread can produce the words of any sample.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint32_t pick(const uint4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// ---------------------------------------------------------------------------
+// Error-free transformation (Knuth TwoSum) and compensated pairs.
+// ---------------------------------------------------------------------------
+struct fpair {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void comp_add(fpair& p, float v) {
+  float s, e;
+  two_sum(p.hi, v, s, e);
+  p.hi = s;
+  p.lo = __fadd_rn(p.lo, e);
+}
+
+__device__ __forceinline__ void comp_merge(fpair& p, const fpair& q) {
+  float s, e;
+  two_sum(p.hi, q.hi, s, e);
+  p.hi = s;
+  p.lo = __fadd_rn(__fadd_rn(p.lo, q.lo), e);
+}
+
+__device__ __forceinline__ double comp_value(const fpair& p) {
+  return (double)p.hi + (double)p.lo;
+}
+
+// ---------------------------------------------------------------------------
+// Precision-generic math.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double vexp(double x) { return exp(x); }
+__device__ __forceinline__ float vexp(float x) { return expf(x); }
+__device__ __forceinline__ double vlog(double x) { return log(x); }
+__device__ __forceinline__ float vlog(float x) { return logf(x); }
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float vsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double vatan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float vatan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double vcos(double x) { return cos(x); }
+__device__ __forceinline__ float vcos(float x) { return cosf(x); }
+__device__ __forceinline__ double vsin(double x) { return sin(x); }
+__device__ __forceinline__ float vsin(float x) { return sinf(x); }
+__device__ __forceinline__ void vsincospi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void vsincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ double vpow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float vpow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double vcopysign(double x, double y) { return copysign(x, y); }
+__device__ __forceinline__ float vcopysign(float x, float y) { return copysignf(x, y); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ bool vfinite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool vfinite(float x) { return isfinite(x); }
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// ---------------------------------------------------------------------------
+// Device-resident iteration state (one per context).
+// ---------------------------------------------------------------------------
+struct GState {
+  uint32_t it;          // Philox iteration counter: iterations run so far
+  int done;             // set when the ACC test stops the current call
+  int live;             // latched per pass by k_reduce: 1 if the pass ran
+  int nhist;            // iterations in the combination window
+  int stopped;
+  long long nonfinite;  // non-finite weights in the window
+  long long samples;    // points in the window
+  double acc;           // relative accuracy target of the current call
+  double I, sigma, chi2;
+  double last_I, last_var, last_sw, last_sw2;
+  long long last_nonfinite;
+  double hist[kMaxHist][2];
+};
+
+// Arguments of the sampling kernel (steps 2-4).
+struct SampleArgs {
+  int d, N, g, ybits;
+  int lanes;               // lanes per hypercube (stratified mode)
+  int strat;
+  int flush_rounds;        // FP32 histogram flush cadence (compensated mode)
+  uint32_t key0, key1, instance;
+  int it_override;         // >= 0: use this iteration index
+  uint64_t ncall;
+  uint64_t nc;             // points per hypercube
+  uint64_t ncubes;
+  int g_pow2, g_log2;
+  int nparts;              // number of CTAs == partial rows
+  const void* tab;         // [d][N] (e_k, Delta_k) in the kernel precision
+  const double* dparams;   // derived integrand constants
+  const GState* st;
+  double* part_bins;       // [2 d N][nparts]
+  double* part_tot;        // [kTotCols][nparts]
+  double* cubes;           // [ncubes][2] or nullptr
+};
+
+// Arguments of the reduction and finalisation kernels (steps 4-6).
+struct FinArgs {
+  int d, N, nparts, strat, refine, record;
+  uint64_t ncall;
+  uint64_t ncubes;
+  double scale;            // integrand output scale (RAMBO units)
+  double alpha;
+  const double* part_bins;
+  const double* part_tot;
+  double* bins;            // [2][d][N] reduced, scaled
+  double* tot;             // [kTotCols] reduced, scaled
+  double* edges;           // [d][N+1]
+  double2* tab64;          // [d][N]
+  float2* tab32;           // [d][N]
+  GState* st;
+};
+
+}  // namespace gv

@@ -1,0 +1,229 @@
+// finalize.cu -- steps 4-6 of Sec. 2.1 after the sampling pass, all on the
+// GPU in FP64 (the paper ran them on the host, Sec. 2.2):
+//   k_reduce    fixed-order reduction of the per-CTA partial rows into the
+//               per-bin sums S1, S2 and the iteration totals (one warp per
+//               column; lanes stride the rows, then an xor butterfly);
+//   k_finalize  per axis: grid optimisation (Lepage 1978: smoothing,
+//               log-compression with exponent alpha, rebinning to equal
+//               weight); one more block: the iteration estimate, the
+//               inverse-variance combination, chi^2 and the ACC test.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gv {
+
+__global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
+  GState* st = F.st;
+  const int stop = st->done;  // nobody writes `done` while k_reduce runs
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->live = !stop;
+  if (stop) return;  // the ACC test stopped this call; no sampling pass ran
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int dN = F.d * F.N;
+  const int np = F.nparts;
+  const double* src;
+  double sc;
+  double* dst;
+  if (col < 2 * dN) {
+    src = F.part_bins + (size_t)col * np;
+    sc = col < dN ? F.scale : F.scale * F.scale;
+    dst = F.bins + col;
+  } else if (col < 2 * dN + 5) {
+    const int q = col - 2 * dN;
+    src = F.part_tot + (size_t)q * np;
+    sc = (q == TOT_SW || q == TOT_SI) ? F.scale
+         : (q == TOT_NONFINITE ? 1.0 : F.scale * F.scale);
+    dst = F.tot + q;
+  } else {
+    return;
+  }
+  double acc = 0.0;
+  for (int r = lane; r < np; r += 32) acc += src[r];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) *dst = acc * sc;
+}
+
+// Neumaier compensated accumulation (same scheme as the CPU oracle).
+struct KSum {
+  double s = 0.0, c = 0.0;
+  __device__ void add(double v) {
+    const double t = s + v;
+    if (fabs(s) >= fabs(v))
+      c += (s - t) + v;
+    else
+      c += (v - t) + s;
+    s = t;
+  }
+  __device__ double value() const { return s + c; }
+};
+
+__device__ void refine_axis(const FinArgs& F, int a) {
+  __shared__ double dsm[kMaxBins], r[kMaxBins], e[kMaxBins + 1], enew[kMaxBins + 1];
+  __shared__ int skip;
+  const int N = F.N, tid = threadIdx.x;
+  const double* dd = F.bins + (size_t)F.d * N + (size_t)a * N;  // S2[a][*]
+  double* ea = F.edges + (size_t)a * (N + 1);
+  for (int k = tid; k <= N; k += blockDim.x) e[k] = ea[k];
+  for (int k = tid; k < N; k += blockDim.x) {
+    double v;
+    if (N == 2)
+      v = (dd[0] + dd[1]) / 2.0;
+    else if (k == 0)
+      v = (dd[0] + dd[1]) / 2.0;
+    else if (k == N - 1)
+      v = (dd[N - 2] + dd[N - 1]) / 2.0;
+    else
+      v = (dd[k - 1] + dd[k] + dd[k + 1]) / 3.0;
+    dsm[k] = v;
+  }
+  __syncthreads();
+  __shared__ double D;
+  if (tid == 0) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) s += dsm[k];
+    D = s;
+    skip = !(s > 0.0) || !isfinite(s);
+  }
+  __syncthreads();
+  if (skip) return;
+  for (int k = tid; k < N; k += blockDim.x) {
+    const double x = dsm[k];
+    r[k] = x <= 0.0 ? 0.0 : (x >= D ? 1.0 : pow((1.0 - x / D) / log(D / x), F.alpha));
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double R = 0.0;
+    for (int k = 0; k < N; ++k) R += r[k];
+    enew[0] = 0.0;
+    enew[N] = 1.0;
+    int k = 0;
+    double acc = 0.0;
+    for (int j = 1; j < N; ++j) {
+      const double tau = (double)j * R / (double)N;
+      while (k < N - 1 && acc + r[k] < tau) {
+        acc += r[k];
+        ++k;
+      }
+      enew[j] = e[k] + (tau - acc) / r[k] * (e[k + 1] - e[k]);
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k <= N; k += blockDim.x) ea[k] = enew[k];
+  for (int k = tid; k < N; k += blockDim.x) {
+    const double lo = enew[k], w = enew[k + 1] - enew[k];
+    F.tab64[(size_t)a * N + k] = make_double2(lo, w);
+    F.tab32[(size_t)a * N + k] = make_float2((float)lo, (float)w);
+  }
+}
+
+__device__ void record_iteration(const FinArgs& F) {
+  GState* st = F.st;
+  const double* t = F.tot;
+  double I, var;
+  if (F.strat) {
+    const double G = (double)F.ncubes;
+    I = t[TOT_SI] / G;
+    var = t[TOT_SV] / (G * G);
+  } else {
+    const double n = (double)F.ncall;
+    I = t[TOT_SW] / n;
+    var = (t[TOT_SW2] / n - I * I) / (n - 1.0);
+    if (var < 0.0) var = 0.0;
+  }
+  st->last_I = I;
+  st->last_var = var;
+  st->last_sw = t[TOT_SW];
+  st->last_sw2 = t[TOT_SW2];
+  st->last_nonfinite = (long long)t[TOT_NONFINITE];
+  if (!F.record) return;
+  int h = st->nhist;
+  if (h < kMaxHist) {
+    st->hist[h][0] = I;
+    st->hist[h][1] = var;
+    st->nhist = ++h;
+  }
+  st->nonfinite += (long long)t[TOT_NONFINITE];
+  st->samples += (long long)F.ncall;
+  st->it += 1;
+  // Inverse-variance combination over the window (Lepage).
+  int nzero = 0;
+  KSum z;
+  for (int j = 0; j < h; ++j)
+    if (!(st->hist[j][1] > 0.0)) {
+      z.add(st->hist[j][0]);
+      ++nzero;
+    }
+  double Ib = 0.0, sg = 0.0, chi = 0.0;
+  if (nzero > 0) {
+    Ib = z.value() / (double)nzero;
+  } else if (h > 0) {
+    KSum sw, swi;
+    for (int j = 0; j < h; ++j) {
+      sw.add(1.0 / st->hist[j][1]);
+      swi.add(st->hist[j][0] / st->hist[j][1]);
+    }
+    Ib = swi.value() / sw.value();
+    sg = 1.0 / sqrt(sw.value());
+    if (h > 1) {
+      KSum c2;
+      for (int j = 0; j < h; ++j) {
+        const double dv = st->hist[j][0] - Ib;
+        c2.add(dv * dv / st->hist[j][1]);
+      }
+      chi = c2.value() / (double)(h - 1);
+    }
+  }
+  st->I = Ib;
+  st->sigma = sg;
+  st->chi2 = chi;
+  if (st->acc > 0.0 && sg < st->acc * fabs(Ib)) {
+    st->done = 1;
+    st->stopped = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const FinArgs F) {
+  // `live` was latched by k_reduce of this pass; the ACC test below writes
+  // only `done`, so every block sees the same decision.
+  if (!F.st->live) return;
+  if ((int)blockIdx.x < F.d) {
+    if (F.refine) refine_axis(F, blockIdx.x);
+  } else if (threadIdx.x == 0) {
+    record_iteration(F);
+  }
+}
+
+// Pure table rebuild (after vegas_set_grid): tab64 / tab32 from edges.
+__global__ void k_tables(const double* edges, int d, int N, double2* tab64, float2* tab32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d * N) return;
+  const int a = i / N, k = i % N;
+  const double lo = edges[(size_t)a * (N + 1) + k], w = edges[(size_t)a * (N + 1) + k + 1] - lo;
+  tab64[i] = make_double2(lo, w);
+  tab32[i] = make_float2((float)lo, (float)w);
+}
+
+}  // namespace gv
+
+extern "C" {
+
+cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s) {
+  const int cols = 2 * F->d * F->N + 5;
+  const int wpb = 8;
+  gv::k_reduce<<<(cols + wpb - 1) / wpb, 32 * wpb, 0, s>>>(*F);
+  return cudaGetLastError();
+}
+
+cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s) {
+  gv::k_finalize<<<F->d + 1, 64, 0, s>>>(*F);
+  return cudaGetLastError();
+}
+
+cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,
+                             cudaStream_t s) {
+  const int n = d * N;
+  gv::k_tables<<<(n + 255) / 256, 256, 0, s>>>(edges, d, N, t64, t32);
+  return cudaGetLastError();
+}
+}

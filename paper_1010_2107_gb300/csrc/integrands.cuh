@@ -1,0 +1,219 @@
+// integrands.cuh -- step 3 (Sec. 2.1) on the device: the integrand registry.
+//
+// Each integrand reads its constants from shared memory (`P`, already in the
+// kernel precision T) as prepared on the host by derive_params() in abi.cu,
+// and takes the mapped point x[0..d) in registers.  DM is the compile-time
+// bound on d (loops are unrolled to DM with a guard on the runtime d).
+#pragma once
+
+#include "common.cuh"
+
+namespace gv {
+
+// Derived-constant slots.  Genz / Gaussian: a-like values at [0, DM),
+// u-like values at [kMaxDim, kMaxDim + d), scalars from kScalar on.
+constexpr int kScalar = 2 * kMaxDim;
+
+// ----------------------------------------------------------------- Genz
+// f = exp(-sum a_i^2 (x_i - u_i)^2).  P[i] = a_i^2, P[kMaxDim+i] = u_i.
+template <typename T, int DM>
+struct GenzGaussian {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    T q = T(0);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t = x[a] - P[kMaxDim + a];
+        q = vfma(P[a] * t, t, q);
+      }
+    return vexp(-q);
+  }
+};
+
+// f = prod (a_i^-2 + (x_i - u_i)^2)^-1.  P[i] = a_i^-2, P[kMaxDim+i] = u_i.
+template <typename T, int DM>
+struct GenzProductPeak {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    T den = T(1);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t = x[a] - P[kMaxDim + a];
+        den *= vfma(t, t, P[a]);
+      }
+    return T(1) / den;
+  }
+};
+
+// f = (1 + sum a_i x_i)^-(d+1).  P[i] = a_i, P[kScalar] = -(d+1).
+template <typename T, int DM>
+struct GenzCornerPeak {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    T t = T(1);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) t = vfma(P[a], x[a], t);
+    return vpow(t, P[kScalar]);
+  }
+};
+
+// f = cos(2 pi u1 + sum a_i x_i).  P[i] = a_i, P[kScalar] = 2 pi u1.
+template <typename T, int DM>
+struct GenzOscillatory {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    T t = P[kScalar];
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) t = vfma(P[a], x[a], t);
+    return vcos(t);
+  }
+};
+
+// Two Gaussian peaks (Lepage's test shape), normalised to unit integral over
+// R^d: f = K/2 (exp(-|x - c1|^2 / w^2) + exp(-|x - c2|^2 / w^2)).
+// P[kScalar + 0..3] = c1, c2, 1/w^2, K/2 with K = (w sqrt pi)^-d.
+template <typename T, int DM>
+struct DoubleGaussian {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    const T c1 = P[kScalar], c2 = P[kScalar + 1];
+    T q1 = T(0), q2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t1 = x[a] - c1, t2 = x[a] - c2;
+        q1 = vfma(t1, t1, q1);
+        q2 = vfma(t2, t2, q2);
+      }
+    const T iw2 = P[kScalar + 2];
+    return P[kScalar + 3] * (vexp(-q1 * iw2) + vexp(-q2 * iw2));
+  }
+};
+
+// ----------------------------------------------------------------- RAMBO
+// Massless n-body phase space (Kleiss, Stirling, Ellis 1986) in units of
+// sqrt(s), with the integrand of include/gvegas.h evaluated dimensionless:
+//   returns  cut * [mu_g / ((s12 - mu)^2 + mu_g^2)] * prod_i 1/s_{i,i+1}
+// (s_ij in units of s, mu = M^2/s, mu_g = M Gamma / s); the host multiplies
+// every sum by the constant V_n s^-3 (or the observable's own scale).
+// Invariants are formed as s_ij = 4 pT_i pT_j (sinh^2(deta/2) + sin^2(dphi/2)),
+// which has no cancellation for nearly collinear pairs in FP32.
+enum {
+  RB_N = kScalar, RB_MU, RB_MUG, RB_MUG2, RB_PTMIN, RB_DR2, RB_CUT, RB_T,
+  RB_INVWC, RB_OBS
+};
+
+template <typename T, int DM>
+struct RamboBW {
+  static constexpr int NM = DM / 4;
+
+  struct Event {
+    T pt[NM], eta[NM], phi[NM];
+  };
+
+  // Momenta -> (pT, eta, phi).  Returns false for a zero-weight point.
+  static __device__ __forceinline__ bool kinematics(const T (&x)[DM], int n, Event& ev) {
+    T E[NM], px[NM], py[NM], pz[NM];
+    T Q0 = T(0), Qx = T(0), Qy = T(0), Qz = T(0);
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      if (i < n) {
+        const T r1 = x[4 * i], r2 = x[4 * i + 1], r3 = x[4 * i + 2], r4 = x[4 * i + 3];
+        if (!(r1 > T(0) && r2 > T(0))) return false;
+        const T q0 = -(vlog(r1) + vlog(r2));
+        const T c = T(2) * r3 - T(1);
+        const T sn = T(2) * vsqrt(r3 * (T(1) - r3));
+        T sp, cp;
+        vsincospi(T(2) * r4, &sp, &cp);
+        E[i] = q0;
+        px[i] = q0 * sn * cp;
+        py[i] = q0 * sn * sp;
+        pz[i] = q0 * c;
+        Q0 += E[i];
+        Qx += px[i];
+        Qy += py[i];
+        Qz += pz[i];
+      }
+    const T MQ = vsqrt((Q0 - Qz) * (Q0 + Qz) - Qx * Qx - Qy * Qy);
+    const T iM = T(1) / MQ;
+    const T bx = -Qx * iM, by = -Qy * iM, bz = -Qz * iM;
+    const T gam = Q0 * iM;
+    const T A = T(1) / (T(1) + gam);
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      if (i < n) {
+        const T bq = bx * px[i] + by * py[i] + bz * pz[i];
+        const T ab = A * bq + E[i];
+        const T qx = iM * vfma(ab, bx, px[i]);
+        const T qy = iM * vfma(ab, by, py[i]);
+        const T qz = iM * vfma(ab, bz, pz[i]);
+        const T pt2 = qx * qx + qy * qy;
+        const T pt = vsqrt(pt2);
+        const T pa = vsqrt(vfma(qz, qz, pt2));
+        ev.pt[i] = pt;
+        ev.eta[i] = vcopysign(vlog((fabs(qz) + pa) / pt), qz);
+        ev.phi[i] = vatan2(qy, qx);
+      }
+    return true;
+  }
+
+  static __device__ __forceinline__ T sij(const Event& ev, int i, int j) {
+    const T he = T(0.5) * (ev.eta[i] - ev.eta[j]);
+    const T eh = vexp(he);
+    const T sh = T(0.5) * (eh - T(1) / eh);
+    const T sp = vsin(T(0.5) * (ev.phi[i] - ev.phi[j]));
+    return T(4) * ev.pt[i] * ev.pt[j] * vfma(sh, sh, sp * sp);
+  }
+
+  static __device__ __forceinline__ T bw(T s12, const T* P) {
+    const T t = s12 - P[RB_MU];
+    return P[RB_MUG] / vfma(t, t, P[RB_MUG2]);
+  }
+
+  static __device__ __forceinline__ T wrap_dphi(T dp) {
+    const T pi = T(3.14159265358979323846);
+    if (dp > pi) dp -= T(2) * pi;
+    if (dp < -pi) dp += T(2) * pi;
+    return dp;
+  }
+
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    const int obs = (int)P[RB_OBS];
+    if (obs == 1) return T(1);
+    const int n = d >> 2;
+    Event ev;
+    if (!kinematics(x, n, ev)) return T(0);
+    const int cut = (int)P[RB_CUT];
+    T cw = T(1);
+    if (obs == 0 && cut == 0) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n && !(ev.pt[i] > P[RB_PTMIN])) return T(0);
+    } else if (obs == 0 && cut == 1) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) cw *= T(1) / (T(1) + vexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
+    }
+    if (obs == 0 && cut != 2) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NM; ++j)
+          if (j < n) {
+            const T de = ev.eta[i] - ev.eta[j];
+            const T dp = wrap_dphi(ev.phi[i] - ev.phi[j]);
+            if (!(vfma(de, de, dp * dp) > P[RB_DR2])) return T(0);
+          }
+    }
+    const T s12 = sij(ev, 0, 1);
+    if (obs == 2) return s12;
+    const T b = bw(s12, P);
+    if (obs == 3) return b;
+    T den = s12;
+#pragma unroll
+    for (int i = 1; i < NM; ++i)
+      if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
+    return cw * b / den;
+  }
+};
+
+}  // namespace gv

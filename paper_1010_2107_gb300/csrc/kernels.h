@@ -1,0 +1,48 @@
+// kernels.h -- host-side view of the device kernels: per-integrand kernel
+// registry (filled by the inst_*.cu translation units) and the launchers of
+// the reduction / finalisation kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace gv {
+
+// One compiled sampling kernel and its companions for a (kind, precision, DM).
+struct KernelEntry {
+  const void* sample;                 // k_sample<T, DM, F, ACC>
+  const void* dump;                   // k_dump<T, DM, F>
+  size_t (*smem)(int d, int N);       // dynamic shared memory of `sample`
+  int dm;                             // compile-time dimension bound
+};
+
+// Per-kind registries; return false when no instantiation covers (prec, d).
+bool entries_genz_gaussian(int prec, int d, KernelEntry* out);
+bool entries_genz_product_peak(int prec, int d, KernelEntry* out);
+bool entries_genz_corner_peak(int prec, int d, KernelEntry* out);
+bool entries_genz_oscillatory(int prec, int d, KernelEntry* out);
+bool entries_dgauss(int prec, int d, KernelEntry* out);
+bool entries_rambo(int prec, int d, KernelEntry* out);
+
+// Arguments of the per-sample dump kernel.
+struct DumpArgs {
+  SampleArgs S;
+  const uint64_t* s;
+  long long n;
+  uint32_t* words;
+  int32_t* bins;
+  double* x;
+  double* jac;
+  double* f;
+};
+
+}  // namespace gv
+
+extern "C" {
+cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s);
+cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s);
+cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,
+                             cudaStream_t s);
+}

@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in include/gvegas.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing
+but convert arguments and results; all steps of the integration run in the CUDA
+library ``_build/libgvegas.so``.  There is no CPU fallback: if the library is
+missing or fails to load, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgvegas.so")
+
+# vegas_status
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, ESTATE = range(7)
+# vegas_integrand_kind
+GENZ_GAUSSIAN, GENZ_PRODUCT_PEAK, GENZ_CORNER_PEAK, GENZ_OSCILLATORY, DOUBLE_GAUSSIAN, RAMBO_BW = range(6)
+# vegas_precision
+FP64, FP32_ACC64, FP32_ACCCOMP = range(3)
+PRECISIONS = {"fp64": FP64, "fp32_acc64": FP32_ACC64, "fp32": FP32_ACCCOMP,
+              "fp32_acccomp": FP32_ACCCOMP}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"gvegas status {status}: {message}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nbins", ctypes.c_int), ("ncall", ctypes.c_int64),
+                ("itmx", ctypes.c_int), ("acc", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("nstrat", ctypes.c_int), ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint32),
+                ("precision", ctypes.c_int), ("ybits", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class IntegrandDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ndim", ctypes.c_int),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("nparams", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_double), ("sigma", ctypes.c_double), ("chi2_dof", ctypes.c_double),
+                ("iters_done", ctypes.c_int), ("stopped", ctypes.c_int),
+                ("nonfinite", ctypes.c_int64), ("samples", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "vegas_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
+                                    ctypes.POINTER(_P)]),
+    "vegas_destroy": (None, [_P]),
+    "vegas_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result)]),
+    "vegas_reset_results": (ctypes.c_int, [_P]),
+    "bases_integrate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_double, ctypes.POINTER(Result),
+                                       ctypes.POINTER(Result)]),
+    "vegas_get_grid": (ctypes.c_int, [_P, _DP, _DP]),
+    "vegas_set_grid": (ctypes.c_int, [_P, _DP]),
+    "vegas_get_history": (ctypes.c_int, [_P, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "vegas_get_cube_sums": (ctypes.c_int, [_P, _DP]),
+    "vegas_get_iteration": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "vegas_set_iteration": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "vegas_set_params": (ctypes.c_int, [_P, _DP, ctypes.c_int]),
+    "vegas_eval": (ctypes.c_int, [_P, ctypes.c_uint32, _DP, _DP]),
+    "vegas_grad": (ctypes.c_int, [_P, ctypes.c_uint32, _DP, _DP]),
+    "vegas_ntheta": (ctypes.c_int, [_P]),
+    "vegas_sample_dump": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32),
+                                         ctypes.POINTER(ctypes.c_int32), _DP, _DP, _DP]),
+    "vegas_set_launch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "vegas_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "vegas_last_error": (ctypes.c_char_p, [_P]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgvegas.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                                  "(run __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _check(st: int, handle=None):
+    if st != OK:
+        msg = lib().vegas_last_error(handle)
+        raise VegasError(st, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # a torch.cuda.Stream
+
+
+class Context:
+    """Owner of one vegas_ctx handle."""
+
+    def __init__(self, handle, ndim, nbins, ncall, nstrat, ybits):
+        self.handle = handle
+        self.ndim, self.nbins, self.ncall, self.nstrat, self.ybits = ndim, nbins, ncall, nstrat, ybits
+
+    def close(self):
+        if self.handle:
+            lib().vegas_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def vegas_create(kind: int, ndim: int, params, *, nbins: int = 50, ncall: int = 100_000,
+                 itmx: int = 5, acc: float = 0.0, alpha: float = 1.5, nstrat: int = 0,
+                 seed: int = 1, instance: int = 0, precision=FP64, ybits: int = 0,
+                 stream=None) -> Context:
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    cfg = Config(int(ndim), int(nbins), int(ncall), int(itmx), float(acc), float(alpha),
+                 int(nstrat), int(seed), int(instance), int(precision), int(ybits),
+                 _stream_handle(stream))
+    fn = IntegrandDesc(int(kind), int(ndim), _dp(p), len(p))
+    h = _P()
+    _check(lib().vegas_create(ctypes.byref(cfg), ctypes.byref(fn), ctypes.byref(h)))
+    yb = ybits or (53 if precision == FP64 else 24)
+    return Context(h, int(ndim), int(nbins), int(ncall), int(nstrat), yb)
+
+
+def vegas_destroy(ctx: Context):
+    ctx.close()
+
+
+def vegas_iterate(ctx: Context, n_iter: int, refine: bool = True, result: bool = True):
+    r = Result()
+    _check(lib().vegas_iterate(ctx.handle, int(n_iter), int(bool(refine)),
+                               ctypes.byref(r) if result else None), ctx.handle)
+    return r.as_dict() if result else None
+
+
+def vegas_reset_results(ctx: Context):
+    _check(lib().vegas_reset_results(ctx.handle), ctx.handle)
+
+
+def bases_integrate(ctx: Context, itmx1: int, acc1: float, itmx2: int, acc2: float):
+    out, ph1 = Result(), Result()
+    _check(lib().bases_integrate(ctx.handle, int(itmx1), float(acc1), int(itmx2), float(acc2),
+                                 ctypes.byref(out), ctypes.byref(ph1)), ctx.handle)
+    return out.as_dict(), ph1.as_dict()
+
+
+def vegas_get_grid(ctx: Context, bin_sums: bool = False):
+    e = np.zeros((ctx.ndim, ctx.nbins + 1))
+    b = np.zeros((2, ctx.ndim, ctx.nbins)) if bin_sums else None
+    _check(lib().vegas_get_grid(ctx.handle, _dp(e), _dp(b) if bin_sums else None), ctx.handle)
+    return (e, b) if bin_sums else e
+
+
+def vegas_set_grid(ctx: Context, edges):
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    if e.shape != (ctx.ndim, ctx.nbins + 1):
+        raise ValueError(f"edges must have shape {(ctx.ndim, ctx.nbins + 1)}")
+    _check(lib().vegas_set_grid(ctx.handle, _dp(e)), ctx.handle)
+
+
+def vegas_get_history(ctx: Context, max_iters: int = 4096):
+    h = np.zeros((max_iters, 2))
+    n = ctypes.c_int()
+    _check(lib().vegas_get_history(ctx.handle, _dp(h), int(max_iters), ctypes.byref(n)), ctx.handle)
+    return h[:min(n.value, max_iters)]
+
+
+def vegas_get_cube_sums(ctx: Context):
+    G = max(ctx.nstrat, 1) ** ctx.ndim
+    c = np.zeros((G, 2))
+    _check(lib().vegas_get_cube_sums(ctx.handle, _dp(c)), ctx.handle)
+    return c
+
+
+def vegas_get_iteration(ctx: Context) -> int:
+    it = ctypes.c_uint32()
+    _check(lib().vegas_get_iteration(ctx.handle, ctypes.byref(it)), ctx.handle)
+    return it.value
+
+
+def vegas_set_iteration(ctx: Context, it: int):
+    _check(lib().vegas_set_iteration(ctx.handle, int(it)), ctx.handle)
+
+
+def vegas_set_params(ctx: Context, params):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    _check(lib().vegas_set_params(ctx.handle, _dp(p), len(p)), ctx.handle)
+
+
+def vegas_eval(ctx: Context, it: int):
+    I, v = ctypes.c_double(), ctypes.c_double()
+    _check(lib().vegas_eval(ctx.handle, int(it), ctypes.byref(I), ctypes.byref(v)), ctx.handle)
+    return I.value, v.value
+
+
+def vegas_ntheta(ctx: Context) -> int:
+    return lib().vegas_ntheta(ctx.handle)
+
+
+def vegas_grad(ctx: Context, it: int):
+    g = np.zeros(max(vegas_ntheta(ctx), 1))
+    I = ctypes.c_double()
+    _check(lib().vegas_grad(ctx.handle, int(it), _dp(g), ctypes.byref(I)), ctx.handle)
+    return g[:vegas_ntheta(ctx)], I.value
+
+
+def vegas_sample_dump(ctx: Context, it: int, s):
+    s = np.ascontiguousarray(s, dtype=np.uint64)
+    n, d = len(s), ctx.ndim
+    W = d if ctx.ybits == 24 else 2 * d
+    words = np.zeros((n, W), np.uint32)
+    bins = np.zeros((n, d), np.int32)
+    x = np.zeros((n, d))
+    jac = np.zeros(n)
+    f = np.zeros(n)
+    _check(lib().vegas_sample_dump(ctx.handle, int(it), s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   n, words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                   bins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   _dp(x), _dp(jac), _dp(f)), ctx.handle)
+    return dict(words=words, bins=bins, x=x, jac=jac, f=f)
+
+
+def vegas_set_launch(ctx: Context, threads: int, ctas_per_sm: int = 0):
+    _check(lib().vegas_set_launch(ctx.handle, int(threads), int(ctas_per_sm)), ctx.handle)
+
+
+def vegas_get_launch(ctx: Context):
+    t, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().vegas_get_launch(ctx.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(o)), ctx.handle)
+    return dict(threads=t.value, ctas=c.value, occupancy=o.value)
+
+
+def vegas_last_error(ctx: Context | None = None) -> str:
+    m = lib().vegas_last_error(ctx.handle if ctx else None)
+    return m.decode() if m else ""

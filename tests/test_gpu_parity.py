@@ -1,0 +1,173 @@
+"""CUDA path against the CPU oracle, through the C ABI, on identical seeded inputs.
+
+Bars (stated per result):
+  * Philox words and grid bins: bit-exact in every precision form.
+  * FP64 form: the Jacobian bit-exact, x within 2 ulp; per-bin sums S1, S2 and the
+    iteration totals within 1e-12 * sum|w| (condition-scaled; the GPU tree
+    order differs from the oracle's sequential Neumaier order); estimates and
+    refined edges within 1e-12 / 1e-13 relative.
+  * FP32 forms (same 24-bit samples as the oracle): estimates within 1e-5
+    relative AND within 0.1 sigma; per-bin sums within 1e-5 * sum|w|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1010_2107_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gv():
+    from paper_1010_2107_gb300 import _build, gvegas
+    _build.build()
+    return gvegas
+
+
+def _pair(gv, orc, kind, d, params, *, N=50, ncall=10000, nstrat=0, precision=0, ybits=0, seed=1):
+    ctx = gv.vegas_create(kind, d, params, nbins=N, ncall=ncall, nstrat=nstrat, precision=precision,
+                          ybits=ybits, seed=seed)
+    cfg = orc.make_cfg(d, nbins=N, ncall=ncall, nstrat=nstrat, ybits=ctx.ybits, seed=seed)
+    fn = orc.Integrand(kind, d, params)
+    return ctx, cfg, fn
+
+
+CASES = [
+    ("gauss4", wl.GENZ_GAUSSIAN, 4, wl.genz_gaussian_params(4), {}),
+    ("pp3", wl.GENZ_PRODUCT_PEAK, 3, np.array([5.0, 3.0, 7.0, 0.3, 0.5, 0.8]), {}),
+    ("cp6", wl.GENZ_CORNER_PEAK, 6, np.array([0.3, 0.1, 0.5, 0.2, 0.4, 0.35]), {}),
+    ("osc5", wl.GENZ_OSCILLATORY, 5, np.array([1.0, 2.0, 0.5, 1.5, 3.0, 0.3]), {}),
+    ("dg8", wl.DOUBLE_GAUSSIAN, 8, wl.double_gaussian_params(), {}),
+    ("rb5", wl.RAMBO_BW, 20, wl.rambo_params(5), {}),
+    ("rb4s", wl.RAMBO_BW, 16, wl.rambo_params(4, cut=1), {}),
+    ("dg4strat", wl.DOUBLE_GAUSSIAN, 4, wl.double_gaussian_params(), dict(nstrat=4, ncall=4 ** 4 * 6)),
+    ("gauss3strat3", wl.GENZ_GAUSSIAN, 3, wl.genz_gaussian_params(3, a=5.0), dict(nstrat=3, ncall=27 * 37)),
+]
+
+
+@pytest.mark.parametrize("name,kind,d,params,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision,ybits", [(0, 53), (0, 24), (2, 24), (1, 53)])
+def test_words_bins_points(gv, orc, name, kind, d, params, kw, precision, ybits):
+    ncall = kw.get("ncall", 3001)
+    ctx, cfg, fn = _pair(gv, orc, kind, d, params, ncall=ncall, nstrat=kw.get("nstrat", 0),
+                         precision=precision, ybits=ybits)
+    with ctx:
+        rng = np.random.default_rng(1)
+        s = np.unique(np.concatenate([[0, 1, ncall - 1], rng.integers(0, ncall, 500)]))
+        for it in (0, 7):
+            g = gv.vegas_sample_dump(ctx, it, s)
+            o = orc.sample_batch(cfg, orc.uniform_grid(d, 50), it, s)
+            assert np.array_equal(g["words"], o["words"])
+            assert np.array_equal(g["bins"], o["bins"])
+            fo = orc.integrand(fn, o["x"]) * o["jac"]
+            fg = g["f"] * g["jac"]
+            if precision == 0:
+                assert np.array_equal(g["jac"], o["jac"])
+                np.testing.assert_allclose(g["x"], o["x"], rtol=4.5e-16, atol=1e-300)
+                ok = np.isclose(fg, fo, rtol=1e-12, atol=1e-300)
+            else:
+                np.testing.assert_allclose(g["x"], o["x"], rtol=0, atol=3e-7)
+                ok = np.isclose(fg, fo, rtol=2e-4, atol=1e-300 + 1e-6 * np.max(np.abs(fo)))
+            # cut decisions may flip for points within rounding of a cut edge
+            assert np.mean(ok) >= (0.99 if kind == wl.RAMBO_BW else 1.0), np.flatnonzero(~ok)[:10]
+
+
+def _cond_close(a, b, scale, tol):
+    return np.all(np.abs(a - b) <= tol * scale)
+
+
+@pytest.mark.parametrize("name,kind,d,params,kw", CASES, ids=[c[0] for c in CASES])
+def test_fp64_iteration_sums(gv, orc, name, kind, d, params, kw):
+    ncall = kw.get("ncall", 20011)
+    ctx, cfg, fn = _pair(gv, orc, kind, d, params, ncall=ncall, nstrat=kw.get("nstrat", 0), precision=0)
+    with ctx:
+        I, var = gv.vegas_eval(ctx, 3)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 3)
+    p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 3, np.arange(ncall))
+    absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    tol = 1e-12 if kind != wl.RAMBO_BW else 1e-9  # RAMBO: cut-edge flips allowed below
+    assert abs(I - o["I"]) <= tol * max(absw.mean(), 1e-300)
+    assert abs(math.sqrt(var) - math.sqrt(o["var"])) <= 1e-9 * math.sqrt(o["var"]) + 1e-300
+    assert _cond_close(bins[0], o["S1"], absw.sum(), tol)
+    assert _cond_close(bins[1], o["S2"], (absw ** 2).sum(), tol)
+
+
+@pytest.mark.parametrize("name,kind,d,params,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_iteration_vs_oracle(gv, orc, name, kind, d, params, kw, precision):
+    ncall = kw.get("ncall", 65536 + 77)
+    ctx, cfg, fn = _pair(gv, orc, kind, d, params, ncall=ncall, nstrat=kw.get("nstrat", 0),
+                         precision=precision, ybits=24)
+    with ctx:
+        I, var = gv.vegas_eval(ctx, 2)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 2)
+    sig = math.sqrt(o["var"])
+    assert abs(I - o["I"]) <= 1e-5 * abs(o["I"]) + 1e-300 or kind == wl.GENZ_OSCILLATORY
+    assert abs(I - o["I"]) <= 0.1 * sig + 1e-300
+    assert abs(math.sqrt(var) - sig) <= 1e-3 * sig + 1e-300
+    p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 2, np.arange(ncall))
+    absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    assert _cond_close(bins[0], o["S1"], absw.sum(), 1e-5)
+    assert _cond_close(bins[1], o["S2"], (absw ** 2).sum(), 1e-5)
+
+
+def test_vegas_loop_fp64_gauss4(gv, orc):
+    """The d=4 Gaussian workload (5 x 1e5, FP64): every iteration estimate, the
+    refined grid and the combined result against the oracle's VEGAS loop."""
+    w = wl.WORKLOADS["gauss4"]
+    ctx, cfg, fn = _pair(gv, orc, w["kind"], 4, w["params"], ncall=w["ncall"], precision=0)
+    with ctx:
+        r = gv.vegas_iterate(ctx, w["itmx"], refine=True)
+        hist = gv.vegas_get_history(ctx)
+        edges = gv.vegas_get_grid(ctx)
+        assert gv.vegas_get_iteration(ctx) == w["itmx"]
+    e = orc.uniform_grid(4, 50)
+    ref = orc.vegas(cfg, fn, e, 0, w["itmx"])
+    np.testing.assert_allclose(hist[:, 0], ref["hist"][:, 0], rtol=1e-12)
+    np.testing.assert_allclose(hist[:, 1], ref["hist"][:, 1], rtol=1e-9)
+    np.testing.assert_allclose(edges, e, rtol=0, atol=1e-13)
+    assert r["I"] == pytest.approx(ref["I"], rel=1e-12)
+    assert r["sigma"] == pytest.approx(ref["sigma"], rel=1e-9)
+    assert r["chi2_dof"] == pytest.approx(ref["chi2_dof"], rel=1e-6, abs=1e-9)
+    exact = 9.8696044010286631e-4
+    assert abs(r["I"] - exact) < 4 * r["sigma"]
+
+
+def test_bases_small_fp64_and_cubes(gv, orc):
+    d, g = 4, 4
+    ncall = g ** d * 8
+    p = wl.double_gaussian_params()
+    ctx, cfg, fn = _pair(gv, orc, wl.DOUBLE_GAUSSIAN, d, p, ncall=ncall, nstrat=g, precision=0, ybits=24)
+    with ctx:
+        out, ph1 = gv.bases_integrate(ctx, 3, 0.0, 3, 0.0)
+        cubes = gv.vegas_get_cube_sums(ctx)
+        hist = gv.vegas_get_history(ctx)
+    e = orc.uniform_grid(d, 50)
+    ref = orc.bases(cfg, fn, e, 0, 3, 0.0, 3, 0.0)
+    assert (ph1["iters_done"], out["iters_done"]) == (3, 3)
+    assert out["I"] == pytest.approx(ref["I"], rel=1e-12)
+    assert out["sigma"] == pytest.approx(ref["sigma"], rel=1e-9)
+    np.testing.assert_allclose(hist, ref["hist"][3:], rtol=1e-9)
+    o = orc.iteration(cfg, fn, e, 5, cubes=True)
+    np.testing.assert_allclose(cubes[:, 0], o["C1"], rtol=1e-12, atol=1e-12 * np.abs(o["C1"]).max())
+    np.testing.assert_allclose(cubes[:, 1], o["C2"], rtol=1e-12, atol=1e-12 * np.abs(o["C2"]).max())
+
+
+def test_nonfinite_weights_are_counted(gv):
+    ctx = gv.vegas_create(gv.GENZ_GAUSSIAN, 1, [float("nan"), 0.5], ncall=1000)
+    with ctx:
+        r = gv.vegas_iterate(ctx, 1)
+    assert r["nonfinite"] == 1000 and r["I"] == 0.0
+
+
+def test_acc_stops_early_on_device(gv):
+    ctx = gv.vegas_create(gv.GENZ_CORNER_PEAK, 2, [0.2, 0.3], nbins=20, ncall=4000, acc=1e-3)
+    with ctx:
+        r = gv.vegas_iterate(ctx, 50)
+        it = gv.vegas_get_iteration(ctx)
+    assert r["stopped"] == 1 and r["iters_done"] < 50 and it == r["iters_done"]
+    assert r["sigma"] < 1e-3 * abs(r["I"])
