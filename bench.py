@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 VEGAS / BASES hot path.
+
+Default workload (``dgauss8``): BASES with hypercube stratification (4 divisions
+per axis: 65 536 cubes x 64 points), d = 8 two-peak Gaussian, FP32 map and
+integrand with compensated FP32 / FP64 sums, 50 bins per axis, 5 grid-optimising
++ 5 frozen-grid iterations of NCALL = 2^22 points.  One step = the whole
+two-phase BASES run from the uniform grid (10 iterations, 41.9 M points).
+
+Metric: points (samples) per second through the iteration loop, whole job.
+Also reported: the plain FP64 GPU path on the same points (speed-up), the
+roofline of the sampling kernel, the reduction pass in GB/s, the CPU oracle
+timed on the host, and the end-to-end rate through the C ABI with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica (different Philox instance word,
+so different points) and the rates add up: weak scaling, no collective on the
+data path; a barrier and a max-reduction of the elapsed time only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "samples/sec per VEGAS/BASES iteration vs plain FP64 GPU path; % FP32 peak"
+UNIT = "samples/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+# Algorithmic FP32-pipe operations per point of the sampling kernel (see
+# DESIGN.md, "Roofline"): Philox, word->bin/position, map, integrand, sums.
+ALGO_OPS = {
+    "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, accumulate=8 * 2 + 2 + 12),
+    "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),
+    "rambo5": dict(philox=5 * 10 * 6, bins=20 * 6, map=20 * 3, integrand=5 * 60 + 10 * 8 + 5 * 14 + 10,
+                   accumulate=20 * 2 + 14),
+}
+# DRAM bytes per launch of the sampling kernel from the committed ncu
+# capture (profiles/); None until captured for the current kernel.
+TRAFFIC = {"dgauss8": None}
+
+
+def _workload(name):
+    from paper_1010_2107_gb300 import workloads as wl
+    return wl.WORKLOADS[name]
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    dist.init_process_group(backend="nccl" if _cuda() else "gloo")
+    return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", "0")), dist
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+# --------------------------------------------------------------------- oracle
+
+
+def oracle_rate(name: str, iters_refine: int, iters_frozen: int):
+    """The CPU oracle as it stands, single-threaded, on full-NCALL BASES
+    iterations of the workload; returns (points/s, points, seconds)."""
+    import oracle
+    w = _workload(name)
+    d = w["ndim"]
+    cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
+                          seed=w["seed"])
+    fn = oracle.Integrand(w["kind"], d, w["params"])
+    e = oracle.uniform_grid(d, w["nbins"])
+    t = time.perf_counter()
+    if w.get("mode") == "bases":
+        oracle.bases(cfg, fn, e, 0, iters_refine, 0.0, iters_frozen, 0.0)
+    else:
+        oracle.vegas(cfg, fn, e, 0, iters_refine + iters_frozen)
+    dt = time.perf_counter() - t
+    n = w["ncall"] * (iters_refine + iters_frozen)
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    rank, world, _, dist = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    name = args.workload
+    w = _workload(name)
+    for _ in range(args.warmup):
+        oracle_rate(name, 1, 0)
+    times = []
+    for _ in range(args.steps):
+        _, n, dt = oracle_rate(name, 1, 0)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * w["ncall"] / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(name),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one grid-optimising iteration of NCALL={w['ncall']} per step, "
+                                   "single-threaded FP64 C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(name):
+    w = _workload(name)
+    c = {"workload": name, "ndim": w["ndim"], "nbins": w["nbins"], "ncall": w["ncall"],
+         "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw"}[w["kind"]],
+         "precision": w["precision"], "ybits": w["ybits"], "nstrat": w["nstrat"],
+         "l2": "flushed between steps (512 MiB write)"}
+    if w.get("mode") == "bases":
+        c["iterations"] = f"{w['itmx1']}+{w['itmx2']} (BASES)"
+    else:
+        c["iterations"] = w.get("itmx")
+    return c
+
+
+# ------------------------------------------------------------------------ ours
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1010_2107_gb300 import _build
+    from paper_1010_2107_gb300 import gvegas as gv
+
+    rank, world, local, dist = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    _build.build()
+    name = args.workload
+    w = _workload(name)
+    d, N, ncall = w["ndim"], w["nbins"], w["ncall"]
+    bases = w.get("mode") == "bases"
+    iters = (w["itmx1"] + w["itmx2"]) if bases else w["itmx"]
+    points_per_step = ncall * iters
+    # A dedicated stream: the library orders its work on it and the events
+    # below are recorded on it (torch's default stream has handle 0, which
+    # the library would replace by a stream of its own).
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec = {"fp32": gv.FP32_ACCCOMP, "fp32_acc64": gv.FP32_ACC64, "fp64": gv.FP64}[args.precision or w["precision"]]
+
+    def make(precision):
+        return gv.vegas_create(w["kind"], d, w["params"], nbins=N, ncall=ncall, nstrat=w["nstrat"],
+                               seed=w["seed"], instance=rank, precision=precision, ybits=w["ybits"],
+                               stream=stream)
+
+    def step(ctx):
+        gv.vegas_reset_grid(ctx)
+        if bases:
+            gv.bases_integrate(ctx, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
+        else:
+            gv.vegas_reset_results(ctx)
+            gv.vegas_iterate(ctx, w["itmx"], refine=True, result=False)
+
+    launches_per_step = 2 + (2 if bases else 2) + 3 * iters
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(ctx, k, warm):
+        for _ in range(warm):
+            step(ctx)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            step(ctx)
+            b.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    ctx = make(prec)
+    with ClockSampler(local) as clk:
+        step_ms = timed(ctx, args.steps, args.warmup)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * points_per_step * args.steps / (total_ms / 1e3)
+    res = gv.vegas_iterate(ctx, 0, refine=False)  # result of the last step (reads back)
+
+    # kernel-level timing on the launching stream: roofline of the sampling kernel
+    peaks, peak_src = _measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    prof = gv.vegas_profile_pass(ctx, 20)
+    launch = gv.vegas_get_launch(ctx)
+    ops = ALGO_OPS.get(name)
+    roof = None
+    if ops:
+        ops_pt = sum(ops.values())
+        achieved = ops_pt * ncall / (prof["sample"] * 1e-3) / 1e12
+        peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        tr = TRAFFIC.get(name)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": tr,
+                "kernel": "k_sample", "ops_per_point": ops_pt, "ms_per_launch": prof["sample"],
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                              f"({peak_src} max clock)"}
+    red_bytes = 8 * (2 * d * N + 5) * launch["ctas"] + 8 * (2 * d * N + 5)
+    reduction = {"kernel": "k_reduce", "bytes_per_launch": red_bytes, "ms_per_launch": prof["reduce"],
+                 "achieved_gbs": red_bytes / (prof["reduce"] * 1e-3) / 1e9,
+                 "peak_gbs": peaks.get("hbm_gbs"), "finalize_ms": prof["finalize"]}
+
+    # plain FP64 GPU path on the same points (speed-up denominator)
+    fp64 = None
+    if not args.no_fp64 and prec != gv.FP64:
+        c64 = make(gv.FP64)
+        k64 = max(3, args.steps // 4)
+        ms64 = timed(c64, k64, 2)
+        r64 = gv.vegas_iterate(c64, 0, refine=False)
+        fp64 = {"value": points_per_step * k64 / (sum(ms64) / 1e3), "unit": UNIT, "steps": k64,
+                "I": r64["I"], "sigma": r64["sigma"],
+                "sample_kernel_ms": gv.vegas_profile_pass(c64, 5)["sample"]}
+        fp64["speedup"] = (value / world) / fp64["value"]
+        c64.close()
+
+    # end to end through the C ABI with host buffers: grid and parameters
+    # uploaded from host memory, the result read back, every step.
+    edges0 = np.tile(np.arange(N + 1, dtype=np.float64) / N, (d, 1))
+    params = np.asarray(w["params"], dtype=np.float64)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        gv.vegas_set_grid(ctx, edges0)
+        gv.vegas_set_params(ctx, params)
+        if bases:
+            out, _ = gv.bases_integrate(ctx, w["itmx1"], 0.0, w["itmx2"], 0.0)
+        else:
+            gv.vegas_reset_results(ctx)
+            out = gv.vegas_iterate(ctx, w["itmx"], refine=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * points_per_step * ke / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": edges0.nbytes + 8 * (2 * 32 + 16),
+           "d2h_bytes_per_step": 160, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, n, dt = oracle_rate(name, 3, 3) if bases else oracle_rate(name, 1, 0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} points: full-NCALL iterations of the same workload "
+                         f"({'3+3 BASES' if bases else '1 VEGAS'}), {dt:.1f} s single-threaded FP64 C oracle"}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != gv.FP64 else "f64",
+            "data": "synthetic", "config": dict(_config(name), accumulation=args.precision or w["precision"],
+                                                launch=launch),
+            "roofline": roof, "reduction": reduction, "fp64_path": fp64, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "result": {"I": res["I"], "sigma": res["sigma"], "chi2_dof": res["chi2_dof"],
+                       "nonfinite": res["nonfinite"]},
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_microbench():
+    import torch
+
+    from paper_1010_2107_gb300 import _build
+    from paper_1010_2107_gb300 import gvegas as gv
+    _build.build()
+    props = torch.cuda.get_device_properties(0)
+    out = {"device": props.name, "sms": props.multi_processor_count, "unit": "thread-ops/s"}
+    for op, name in gv.MICROBENCH_OPS.items():
+        out[name] = gv.vegas_microbench(op)
+    per_sm_clk = {}
+    with ClockSampler(0) as clk:
+        for op, name in gv.MICROBENCH_OPS.items():
+            gv.vegas_microbench(op)
+    c = clk.summary()
+    mhz = c.get("sm_mhz") or 2070.0
+    for op, name in gv.MICROBENCH_OPS.items():
+        per_sm_clk[name] = out[name] / (props.multi_processor_count * mhz * 1e6)
+    out["per_sm_per_clock"] = per_sm_clk
+    out["clocks"] = c
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dgauss8", choices=["dgauss8", "gauss4", "rambo5"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--microbench", action="store_true",
+                    help="print the measured instruction-class rates (ALU roofline denominators)")
+    args = ap.parse_args()
+    if args.microbench:
+        return run_microbench()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

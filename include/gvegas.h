@@ -162,13 +162,20 @@ vegas_status vegas_iterate(vegas_ctx* ctx, int n_iter, int refine,
                            vegas_result* out);
 
 /* Start a new combination window (the grid and the iteration counter are
- * kept). */
+ * kept).  Stream-ordered, no synchronisation. */
 vegas_status vegas_reset_results(vegas_ctx* ctx);
+
+/* Put back the uniform grid e_a[k] = k/N of step 1 (device-side,
+ * stream-ordered, no synchronisation). */
+vegas_status vegas_reset_grid(vegas_ctx* ctx);
 
 /* BASES (Sec. 2.1 and Sec. 5.1): a grid-optimisation phase of up to itmx1
  * refining iterations (stopping at acc1), then an integration phase of up
- * to itmx2 iterations on the frozen grid (stopping at acc2).  out receives
- * the integration phase alone; phase1 (nullable) the first phase. */
+ * to itmx2 iterations on the frozen grid (stopping at acc2).  Both phases
+ * run as one CUDA graph with the ACC tests on the device.  out receives the
+ * integration phase alone, phase1 the first phase; when both are NULL the
+ * call returns without synchronising (results stay readable through
+ * vegas_iterate(ctx, 0, 0, &r) or vegas_get_history). */
 vegas_status bases_integrate(vegas_ctx* ctx, int itmx1, double acc1,
                              int itmx2, double acc2, vegas_result* out,
                              vegas_result* phase1);
@@ -229,6 +236,29 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
 vegas_status vegas_set_launch(vegas_ctx* ctx, int threads, int ctas_per_sm);
 vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
                               int* ctas_per_sm);
+
+/* Measurement (the paper times whole programs, Sec. 3.3; this times each
+ * kernel): runs n_pass evaluation passes at the current iteration index
+ * (no refinement, window untouched) with CUDA events recorded on the
+ * context stream around each kernel, and returns the mean milliseconds per
+ * launch of ms[0] the sampling kernel, ms[1] the reduction, ms[2] the
+ * finalisation.  Synchronises the stream. */
+vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
+
+/* Measured issue rate of one instruction class on the current device, in
+ * thread-operations per second summed over all SMs (no counterpart in the
+ * paper; these are the denominators of the ALU roofline).  op: 0 FP32 FMA,
+ * 1 32x32->64 integer multiply pair (mul.hi + mul.lo, counted as one),
+ * 2 FP64 FMA, 3 exp2 on the special-function unit, 4 u32->f32 conversion,
+ * 5 Philox4x32-10 blocks, 6 shared-memory float atomicAdd into one
+ * 50-bin histogram per CTA, 7 the same with one histogram per warp,
+ * 8 32-bit integer shared atomicAdd, 9 double shared atomicAdd,
+ * 10 Philox blocks with 64-bit products, 11 warp shuffles, 12 bin
+ * updates by warp ownership (8 axes, 50 bins, shuffles, no atomics),
+ * 13 64-bit integer shared atomicAdd (one histogram per CTA), 14 the same
+ * with one histogram per warp, 15 32-bit integer atomicAdd per warp.
+ * Launches its own kernels on the legacy default stream and synchronises. */
+vegas_status vegas_microbench(int op, double* rate);
 
 /* Message of the last failure on ctx (or of the calling thread when ctx is
  * NULL).  Never NULL. */

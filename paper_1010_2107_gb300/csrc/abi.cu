@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -46,7 +47,8 @@ struct vegas_ctx {
   gv::KernelEntry ke{};
   int sm_count = 0;
   // launch geometry
-  int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, flush_rounds = 1, occ = 0;
+  int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, lanes_req = 0, occ = 0;
+  int cap = 16;  // histogram bucket capacity (see sample_kernel.cuh)
   size_t smem = 0;
   // device buffers
   double* d_edges = nullptr;
@@ -66,7 +68,8 @@ struct vegas_ctx {
   size_t h_stage_len = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  // graph cache, keyed by (shape, n1, n2, refine, acc1, acc2)
+  std::map<std::tuple<int, int, int, int, double, double>, cudaGraphExec_t> graphs;
   int hist_upper = 0;  // upper bound of the window length (host shadow)
   std::string err;
 
@@ -200,14 +203,21 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale,
   }
 }
 
-bool lookup_kernel(int kind, int prec, int d, gv::KernelEntry* e) {
+bool lookup_kernel(int kind, int prec, int ybits, int d, gv::KernelEntry* e) {
+  const bool y24 = ybits == 24;
   switch (kind) {
-    case VG_GENZ_GAUSSIAN: return gv::entries_genz_gaussian(prec, d, e);
-    case VG_GENZ_PRODUCT_PEAK: return gv::entries_genz_product_peak(prec, d, e);
-    case VG_GENZ_CORNER_PEAK: return gv::entries_genz_corner_peak(prec, d, e);
-    case VG_GENZ_OSCILLATORY: return gv::entries_genz_oscillatory(prec, d, e);
-    case VG_DOUBLE_GAUSSIAN: return gv::entries_dgauss(prec, d, e);
-    case VG_RAMBO_BW: return gv::entries_rambo(prec, d, e);
+    case VG_GENZ_GAUSSIAN:
+      return y24 ? gv::entries_genz_gaussian_y24(prec, d, e) : gv::entries_genz_gaussian_y53(prec, d, e);
+    case VG_GENZ_PRODUCT_PEAK:
+      return y24 ? gv::entries_genz_product_peak_y24(prec, d, e) : gv::entries_genz_product_peak_y53(prec, d, e);
+    case VG_GENZ_CORNER_PEAK:
+      return y24 ? gv::entries_genz_corner_peak_y24(prec, d, e) : gv::entries_genz_corner_peak_y53(prec, d, e);
+    case VG_GENZ_OSCILLATORY:
+      return y24 ? gv::entries_genz_oscillatory_y24(prec, d, e) : gv::entries_genz_oscillatory_y53(prec, d, e);
+    case VG_DOUBLE_GAUSSIAN:
+      return y24 ? gv::entries_dgauss_y24(prec, d, e) : gv::entries_dgauss_y53(prec, d, e);
+    case VG_RAMBO_BW:
+      return y24 ? gv::entries_rambo_y24(prec, d, e) : gv::entries_rambo_y53(prec, d, e);
     default: return false;
   }
 }
@@ -221,11 +231,27 @@ void destroy_graphs(vegas_ctx* c) {
 // (or as requested), capped by the work available.
 vegas_status configure_launch(vegas_ctx* c) {
   const int d = c->cfg.ndim, N = c->cfg.nbins;
-  c->smem = c->ke.smem(d, N);
-  CK(c, cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)c->smem));
+  // Bucket capacity per (axis, bin) and tile: about 2.5x the mean fill of a
+  // uniformly spread tile plus 4, a power of two in 4..64; halved until the
+  // CTA's shared memory fits.
+  int cap = 4;
+  while (cap < 64 && cap < (5 * c->threads) / (2 * N) + 4) cap *= 2;
   int occ = 0;
-  CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ke.sample, c->threads, c->smem));
+  for (;;) {
+    c->smem = c->ke.smem(d, N, cap);
+    cudaError_t e = cudaSuccess;
+    occ = 0;
+    if (c->smem <= 227 * 1024) {
+      e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ke.sample, c->threads, c->smem);
+    }
+    if (e != cudaSuccess)
+      return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+    if (occ >= 1 || cap == 1) break;
+    cap /= 2;
+  }
+  c->cap = cap;
   if (occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %zu B smem",
                               c->threads, c->smem);
   c->occ = occ;
@@ -234,23 +260,21 @@ vegas_status configure_launch(vegas_ctx* c) {
   const int64_t cap_threads = cap_ctas * c->threads;
   uint64_t units;
   if (c->strat) {
+    // lanes per hypercube: enough groups for >= 4 rounds of the resident
+    // threads (load balance), at most 32 and at most the points per cube
     int L = 1;
-    while (L < 32 && (uint64_t)(2 * L) <= c->nc && c->ncubes * (uint64_t)(2 * L) <= (uint64_t)cap_threads) L *= 2;
-    c->lanes = L;
-    units = c->ncubes * (uint64_t)L;
+    while (L < 32 && (uint64_t)(2 * L) <= c->nc && c->ncubes * (uint64_t)L < 4 * (uint64_t)cap_threads) L *= 2;
+    if (c->lanes_req > 0) L = std::min<int>(c->lanes_req, (int)std::min<uint64_t>(32, c->nc));
+    int Lp = 1;
+    while (2 * Lp <= L) Lp *= 2;
+    c->lanes = Lp;
+    units = c->ncubes * (uint64_t)Lp;
   } else {
     c->lanes = 1;
     units = (uint64_t)c->cfg.ncall;
   }
   int64_t ctas = (int64_t)((units + c->threads - 1) / c->threads);
   c->ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, cap_ctas));
-  // compensated mode: flush the FP32 histograms after ~4096 points per CTA
-  if (c->strat) {
-    const uint64_t per_round = (uint64_t)(c->threads / c->lanes) * c->nc;
-    c->flush_rounds = (int)std::max<uint64_t>(1, 4096 / std::max<uint64_t>(per_round, 1));
-  } else {
-    c->flush_rounds = std::max(1, 4096 / c->threads);
-  }
   if (c->ctas > c->part_rows) {
     if (c->d_part_bins) cudaFree(c->d_part_bins);
     if (c->d_part_tot) cudaFree(c->d_part_tot);
@@ -272,18 +296,26 @@ gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
   A.g = c->g;
   A.ybits = c->ybits;
   A.lanes = c->lanes;
+  A.cap = c->cap;
   A.strat = c->strat;
-  A.flush_rounds = c->flush_rounds;
   A.key0 = (uint32_t)c->cfg.seed;
   A.key1 = (uint32_t)(c->cfg.seed >> 32);
   A.instance = c->cfg.instance;
   A.it_override = it_override;
   A.ncall = (uint64_t)c->cfg.ncall;
-  A.nc = c->nc;
-  A.ncubes = c->ncubes;
+  A.nc = (uint32_t)c->nc;
+  A.ncubes = (uint32_t)c->ncubes;
+  const bool cubes_pow2 = (c->ncubes & (c->ncubes - 1)) == 0;
+  A.cube_mul = (c->strat && cubes_pow2 && c->ncubes > 1) ? 0x9E3779B1u : 1u;
   A.g_pow2 = (c->g & (c->g - 1)) == 0;
   A.g_log2 = 0;
   while ((1 << A.g_log2) < c->g) ++A.g_log2;
+  A.t32 = (int64_t)c->g * c->cfg.nbins <= 256;
+  const double gb = (double)c->g * std::ldexp(1.0, c->ybits);
+  A.inv_gb_d = 1.0 / gb;
+  A.inv_gb_f = (float)(1.0 / gb);
+  A.inv_nc = c->nc > 0 ? 1.0 / (double)c->nc : 0.0;
+  A.inv_nc1 = c->nc > 1 ? 1.0 / (double)(c->nc - 1) : 0.0;
   A.nparts = c->ctas;
   A.tab = c->prec == VG_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
   A.dparams = c->d_derived;
@@ -302,6 +334,7 @@ gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record) {
   F.strat = c->strat;
   F.refine = refine;
   F.record = record;
+  F.pair32 = c->prec == VG_FP32_ACCCOMP;
   F.ncall = (uint64_t)c->cfg.ncall;
   F.ncubes = c->ncubes;
   F.scale = c->scale;
@@ -328,8 +361,13 @@ vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record) 
   return VEGAS_OK;
 }
 
-vegas_status get_graph(vegas_ctx* c, int n_iter, int refine, cudaGraphExec_t* out) {
-  auto key = std::make_pair(n_iter, refine);
+// Graph of one call.  shape 0 (vegas_iterate): set the ACC target, then n1
+// passes (refining if `refine`).  shape 1 (bases_integrate): reset the
+// window, n1 refining passes at acc1, snapshot phase 1, reset, n2 frozen-grid
+// passes at acc2.  Each call shape is captured once and replayed.
+vegas_status get_graph(vegas_ctx* c, int shape, int n1, int n2, int refine, double acc1, double acc2,
+                       cudaGraphExec_t* out) {
+  auto key = std::make_tuple(shape, n1, n2, refine, acc1, acc2);
   auto itg = c->graphs.find(key);
   if (itg != c->graphs.end()) {
     *out = itg->second;
@@ -338,7 +376,20 @@ vegas_status get_graph(vegas_ctx* c, int n_iter, int refine, cudaGraphExec_t* ou
   cudaGraph_t g = nullptr;
   CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   vegas_status st = VEGAS_OK;
-  for (int i = 0; i < n_iter && st == VEGAS_OK; ++i) st = launch_pass(c, -1, refine, 1);
+  auto ctl = [&](int ops, double acc) {
+    if (st) return;
+    cudaError_t e = gv_launch_control(c->d_st, ops, acc, c->stream);
+    if (e != cudaSuccess) st = c->fail(VEGAS_ECUDA, "control: %s", cudaGetErrorString(e));
+  };
+  if (shape == 0) {
+    ctl(gv::CTL_SET_ACC, acc1);
+    for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, refine, 1);
+  } else {
+    ctl(gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, acc1);
+    for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, 1, 1);
+    ctl(gv::CTL_SNAPSHOT | gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, acc2);
+    for (int i = 0; i < n2 && !st; ++i) st = launch_pass(c, -1, 0, 1);
+  }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (st != VEGAS_OK) {
     if (g) cudaGraphDestroy(g);
@@ -349,6 +400,7 @@ vegas_status get_graph(vegas_ctx* c, int n_iter, int refine, cudaGraphExec_t* ou
   e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  if (c->graphs.size() >= 64) destroy_graphs(c);
   c->graphs[key] = ge;
   *out = ge;
   return VEGAS_OK;
@@ -489,10 +541,13 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
     delete c;
     return thread_fail(VEGAS_EINVAL, "%s", why.c_str());
   }
-  if (!lookup_kernel(fn->kind, c->prec, d, &c->ke)) {
+  if (!lookup_kernel(fn->kind, c->prec, ybits, d, &c->ke)) {
     delete c;
     return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
   }
+  // the specialised kernel when the shape allows it (see kernels.h)
+  if (c->ke.sample_spec && d == c->ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256)
+    c->ke.sample = c->ke.sample_spec;
   auto bail = [&](vegas_status st) {
     g_thread_err = c->err;
     vegas_destroy(c);
@@ -546,19 +601,13 @@ vegas_status vegas_iterate(vegas_ctx* c, int n_iter, int refine, vegas_result* o
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
   if (n_iter < 0) return c->fail(VEGAS_EINVAL, "n_iter < 0");
   if (n_iter > 0) {
-    vegas_status st = VEGAS_OK;
     if (c->hist_upper + n_iter > gv::kMaxHist)
       return c->fail(VEGAS_EINVAL, "window would exceed %d iterations; call vegas_reset_results", gv::kMaxHist);
-    c->hist_upper += n_iter;
-    // per call: clear the stop flag, set this call's ACC target
-    int zero[2] = {0, 0};
-    CK(c, cudaMemcpyAsync(&c->d_st->done, zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaMemcpyAsync(&c->d_st->stopped, zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    double acc = c->cfg.acc;
-    CK(c, cudaMemcpyAsync(&c->d_st->acc, &acc, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     cudaGraphExec_t ge;
-    if ((st = get_graph(c, n_iter, refine ? 1 : 0, &ge))) return st;
+    vegas_status st = get_graph(c, 0, n_iter, 0, refine ? 1 : 0, c->cfg.acc, 0.0, &ge);
+    if (st) return st;
     CK(c, cudaGraphLaunch(ge, c->stream));
+    c->hist_upper += n_iter;
   }
   if (out) {
     vegas_status st = read_state(c);
@@ -570,40 +619,44 @@ vegas_status vegas_iterate(vegas_ctx* c, int n_iter, int refine, vegas_result* o
 
 vegas_status vegas_reset_results(vegas_ctx* c) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  vegas_status st = read_state(c);
-  if (st) return st;
-  GState* h = c->h_st;
-  h->nhist = 0;
-  h->nonfinite = 0;
-  h->samples = 0;
-  h->I = h->sigma = h->chi2 = 0.0;
-  h->done = 0;
-  h->stopped = 0;
+  CK(c, gv_launch_control(c->d_st, gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, c->cfg.acc, c->stream));
   c->hist_upper = 0;
-  CK(c, cudaMemcpyAsync(c->d_st, h, offsetof(GState, hist), cudaMemcpyHostToDevice, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status vegas_reset_grid(vegas_ctx* c) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  const int d = c->cfg.ndim, N = c->cfg.nbins;
+  CK(c, gv_launch_uniform_grid(c->d_edges, d, N, c->stream));
+  CK(c, gv_launch_tables(c->d_edges, d, N, c->d_tab64, c->d_tab32, c->stream));
   return VEGAS_OK;
 }
 
 vegas_status bases_integrate(vegas_ctx* c, int itmx1, double acc1, int itmx2, double acc2,
                              vegas_result* out, vegas_result* phase1) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  if (itmx1 < 0 || itmx2 < 1) return c->fail(VEGAS_EINVAL, "need itmx1 >= 0 and itmx2 >= 1");
-  const double acc_save = c->cfg.acc;
-  vegas_status st = vegas_reset_results(c);
-  vegas_result r1{};
-  if (!st && itmx1 > 0) {
-    c->cfg.acc = acc1;
-    st = vegas_iterate(c, itmx1, 1, phase1 ? &r1 : nullptr);
+  if (itmx1 < 0 || itmx2 < 1 || itmx1 > gv::kMaxHist || itmx2 > gv::kMaxHist)
+    return c->fail(VEGAS_EINVAL, "need 0 <= itmx1 <= %d and 1 <= itmx2 <= %d", gv::kMaxHist, gv::kMaxHist);
+  cudaGraphExec_t ge;
+  vegas_status st = get_graph(c, 1, itmx1, itmx2, 1, acc1, acc2, &ge);
+  if (st) return st;
+  CK(c, cudaGraphLaunch(ge, c->stream));
+  c->hist_upper = itmx2;
+  if (out || phase1) {
+    if ((st = read_state(c))) return st;
+    if (out) fill_result(c, out);
+    if (phase1) {
+      const GState* h = c->h_st;
+      phase1->I = h->ph1_I;
+      phase1->sigma = h->ph1_sigma;
+      phase1->chi2_dof = h->ph1_chi2;
+      phase1->iters_done = h->ph1_iters;
+      phase1->stopped = h->ph1_stopped;
+      phase1->nonfinite = h->ph1_nonfinite;
+      phase1->samples = h->ph1_samples;
+    }
   }
-  if (!st) st = vegas_reset_results(c);
-  if (!st) {
-    c->cfg.acc = acc2;
-    st = vegas_iterate(c, itmx2, 0, out);
-  }
-  c->cfg.acc = acc_save;
-  if (!st && phase1) *phase1 = r1;
-  return st;
+  return VEGAS_OK;
 }
 
 vegas_status vegas_get_grid(vegas_ctx* c, double* edges, double* bin_sums) {
@@ -654,9 +707,16 @@ vegas_status vegas_get_cube_sums(vegas_ctx* c, double* sums) {
   CK(c, cudaMemcpyAsync(c->h_stage, c->d_cubes, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   const double s1 = c->scale, s2 = c->scale * c->scale;
+  const bool pairs = c->prec == VG_FP32_ACCCOMP;  // (hi, lo, hi, lo) floats per cube
+  const float* fp = reinterpret_cast<const float*>(c->h_stage);
   for (size_t i = 0; i < c->ncubes; ++i) {
-    sums[2 * i] = c->h_stage[2 * i] * s1;
-    sums[2 * i + 1] = c->h_stage[2 * i + 1] * s2;
+    if (pairs) {
+      sums[2 * i] = ((double)fp[4 * i] + (double)fp[4 * i + 1]) * s1;
+      sums[2 * i + 1] = ((double)fp[4 * i + 2] + (double)fp[4 * i + 3]) * s2;
+    } else {
+      sums[2 * i] = c->h_stage[2 * i] * s1;
+      sums[2 * i + 1] = c->h_stage[2 * i + 1] * s2;
+    }
   }
   return VEGAS_OK;
 }
@@ -801,6 +861,43 @@ vegas_status vegas_grad(vegas_ctx* c, uint32_t it, double* grad, double* I) {
   (void)I;
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
   return c->fail(VEGAS_EINVAL, "gradient not available for this integrand");
+}
+
+vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (n_pass < 1 || !ms) return c->fail(VEGAS_EINVAL, "need n_pass >= 1 and ms[3]");
+  CK(c, cudaStreamSynchronize(c->stream));
+  vegas_status st = read_state(c);
+  if (st) return st;
+  const uint32_t it = c->h_st->it;
+  int zero = 0;
+  CK(c, cudaMemcpyAsync(&c->d_st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) CK(c, cudaEventCreate(&ev[i]));
+  double acc[3] = {0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < n_pass && e == cudaSuccess; ++p) {
+    gv::SampleArgs A = sample_args(c, (int)(it & 0x7FFFFFFFu));
+    void* args[] = {&A};
+    gv::FinArgs F = fin_args(c, 0, 0);
+    e = cudaEventRecord(ev[0], c->stream);
+    if (!e) e = cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream);
+    if (!e) e = cudaEventRecord(ev[1], c->stream);
+    if (!e) e = gv_launch_reduce(&F, c->stream);
+    if (!e) e = cudaEventRecord(ev[2], c->stream);
+    if (!e) e = gv_launch_finalize(&F, c->stream);
+    if (!e) e = cudaEventRecord(ev[3], c->stream);
+    if (!e) e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && !e; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "profile: %s", cudaGetErrorString(e));
+  for (int k = 0; k < 3; ++k) ms[k] = acc[k] / n_pass;
+  return VEGAS_OK;
 }
 
 int vegas_ntheta(const vegas_ctx* c) {

@@ -120,38 +120,52 @@ struct GState {
   double I, sigma, chi2;
   double last_I, last_var, last_sw, last_sw2;
   long long last_nonfinite;
+  // snapshot of the first BASES phase
+  double ph1_I, ph1_sigma, ph1_chi2;
+  int ph1_iters, ph1_stopped;
+  long long ph1_nonfinite, ph1_samples;
   double hist[kMaxHist][2];
 };
+
+// Device-side control operations captured into the iteration graphs.
+enum { CTL_RESET_WINDOW = 1, CTL_SET_ACC = 2, CTL_SNAPSHOT = 4 };
 
 // Arguments of the sampling kernel (steps 2-4).
 struct SampleArgs {
   int d, N, g, ybits;
-  int lanes;               // lanes per hypercube (stratified mode)
+  int lanes;               // lanes per hypercube (stratified mode), power of two <= 32
+  int cap;                 // bucket capacity per (axis, bin) and tile
   int strat;
-  int flush_rounds;        // FP32 histogram flush cadence (compensated mode)
   uint32_t key0, key1, instance;
   int it_override;         // >= 0: use this iteration index
   uint64_t ncall;
-  uint64_t nc;             // points per hypercube
-  uint64_t ncubes;
+  uint32_t nc;             // points per hypercube
+  uint32_t ncubes;         // number of hypercubes
+  uint32_t cube_mul;       // odd multiplier permuting the cube order (power-of-two
+                           // cube counts; 1 otherwise)
   int g_pow2, g_log2;
+  int t32;                 // 24-bit bins fit 32-bit integers (g N <= 256)
+  float inv_gb_f;          // 1 / (g 2^ybits)
+  double inv_gb_d;
+  double inv_nc, inv_nc1;  // 1 / nc, 1 / (nc - 1)
   int nparts;              // number of CTAs == partial rows
   const void* tab;         // [d][N] (e_k, Delta_k) in the kernel precision
   const double* dparams;   // derived integrand constants
   const GState* st;
-  double* part_bins;       // [2 d N][nparts]
+  void* part_bins;         // [2 d N][nparts]: double, or float (hi, lo) pairs (FP32 forms)
   double* part_tot;        // [kTotCols][nparts]
-  double* cubes;           // [ncubes][2] or nullptr
+  void* cubes;             // [ncubes]: double (sum w, sum w^2), or float (hi, lo, hi, lo)
 };
 
 // Arguments of the reduction and finalisation kernels (steps 4-6).
 struct FinArgs {
   int d, N, nparts, strat, refine, record;
+  int pair32;              // part_bins hold float (hi, lo) pairs
   uint64_t ncall;
   uint64_t ncubes;
   double scale;            // integrand output scale (RAMBO units)
   double alpha;
-  const double* part_bins;
+  const void* part_bins;
   const double* part_tot;
   double* bins;            // [2][d][N] reduced, scaled
   double* tot;             // [kTotCols] reduced, scaled

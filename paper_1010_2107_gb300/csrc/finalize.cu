@@ -24,8 +24,26 @@ __global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
   const double* src;
   double sc;
   double* dst;
+  if (col < 2 * dN && F.pair32) {
+    // compensated FP32 pairs: fixed-order compensated sum, one conversion
+    const float2* p = reinterpret_cast<const float2*>(F.part_bins) + (size_t)col * np;
+    fpair acc{0.f, 0.f};
+    for (int r = lane; r < np; r += 32) {
+      const float2 v = p[r];
+      comp_merge(acc, fpair{v.x, v.y});
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      fpair o;
+      o.hi = __shfl_xor_sync(0xffffffffu, acc.hi, off);
+      o.lo = __shfl_xor_sync(0xffffffffu, acc.lo, off);
+      comp_merge(acc, o);
+    }
+    if (lane == 0) F.bins[col] = comp_value(acc) * (col < dN ? F.scale : F.scale * F.scale);
+    return;
+  }
   if (col < 2 * dN) {
-    src = F.part_bins + (size_t)col * np;
+    src = reinterpret_cast<const double*>(F.part_bins) + (size_t)col * np;
     sc = col < dN ? F.scale : F.scale * F.scale;
     dst = F.bins + col;
   } else if (col < 2 * dN + 5) {
@@ -194,6 +212,37 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs F) {
   }
 }
 
+// Window / stop-flag bookkeeping between passes (one thread).
+__global__ void k_control(GState* st, int ops, double acc) {
+  if (ops & CTL_SNAPSHOT) {
+    st->ph1_I = st->I;
+    st->ph1_sigma = st->sigma;
+    st->ph1_chi2 = st->chi2;
+    st->ph1_iters = st->nhist;
+    st->ph1_stopped = st->stopped;
+    st->ph1_nonfinite = st->nonfinite;
+    st->ph1_samples = st->samples;
+  }
+  if (ops & CTL_RESET_WINDOW) {
+    st->nhist = 0;
+    st->nonfinite = 0;
+    st->samples = 0;
+    st->I = st->sigma = st->chi2 = 0.0;
+  }
+  if (ops & CTL_SET_ACC) {
+    st->acc = acc;
+    st->done = 0;
+    st->stopped = 0;
+  }
+}
+
+// Uniform grid e_a[k] = k / N (step 1).
+__global__ void k_uniform_grid(double* edges, int d, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d * (N + 1)) return;
+  edges[i] = (double)(i % (N + 1)) / (double)N;
+}
+
 // Pure table rebuild (after vegas_set_grid): tab64 / tab32 from edges.
 __global__ void k_tables(const double* edges, int d, int N, double2* tab64, float2* tab32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -217,6 +266,17 @@ cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s) {
 
 cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s) {
   gv::k_finalize<<<F->d + 1, 64, 0, s>>>(*F);
+  return cudaGetLastError();
+}
+
+cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s) {
+  gv::k_control<<<1, 1, 0, s>>>(st, ops, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s) {
+  const int n = d * (N + 1);
+  gv::k_uniform_grid<<<(n + 255) / 256, 256, 0, s>>>(edges, d, N);
   return cudaGetLastError();
 }
 

@@ -10,6 +10,11 @@
 
 namespace gv {
 
+// exp of a non-positive Gaussian exponent: the special-function unit for
+// FP32 (relative error ~2^-21 over the range that matters), libm for FP64.
+__device__ __forceinline__ float gexp(float x) { return __expf(x); }
+__device__ __forceinline__ double gexp(double x) { return exp(x); }
+
 // Derived-constant slots.  Genz / Gaussian: a-like values at [0, DM),
 // u-like values at [kMaxDim, kMaxDim + d), scalars from kScalar on.
 constexpr int kScalar = 2 * kMaxDim;
@@ -26,7 +31,7 @@ struct GenzGaussian {
         const T t = x[a] - P[kMaxDim + a];
         q = vfma(P[a] * t, t, q);
       }
-    return vexp(-q);
+    return gexp(-q);
   }
 };
 
@@ -85,7 +90,7 @@ struct DoubleGaussian {
         q2 = vfma(t2, t2, q2);
       }
     const T iw2 = P[kScalar + 2];
-    return P[kScalar + 3] * (vexp(-q1 * iw2) + vexp(-q2 * iw2));
+    return P[kScalar + 3] * (gexp(-q1 * iw2) + gexp(-q2 * iw2));
   }
 };
 

@@ -12,19 +12,29 @@ namespace gv {
 
 // One compiled sampling kernel and its companions for a (kind, precision, DM).
 struct KernelEntry {
-  const void* sample;                 // k_sample<T, DM, F, ACC>
+  const void* sample;                 // k_sample<T, DM, F, ACC, YB, false> (any d <= DM)
+  const void* sample_spec;            // k_sample<..., true>: d == DM, 24-bit, power-of-two
+                                      // divisions with g N <= 256; may be null
   const void* dump;                   // k_dump<T, DM, F>
-  size_t (*smem)(int d, int N);       // dynamic shared memory of `sample`
+  size_t (*smem)(int d, int N, int cap);  // dynamic shared memory of `sample`
+                                          // with bucket capacity cap
   int dm;                             // compile-time dimension bound
 };
 
-// Per-kind registries; return false when no instantiation covers (prec, d).
-bool entries_genz_gaussian(int prec, int d, KernelEntry* out);
-bool entries_genz_product_peak(int prec, int d, KernelEntry* out);
-bool entries_genz_corner_peak(int prec, int d, KernelEntry* out);
-bool entries_genz_oscillatory(int prec, int d, KernelEntry* out);
-bool entries_dgauss(int prec, int d, KernelEntry* out);
-bool entries_rambo(int prec, int d, KernelEntry* out);
+// Per-kind registries (one per random-bit width); false when no
+// instantiation covers (precision, d).
+bool entries_genz_gaussian_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_gaussian_y53(int prec, int d, KernelEntry* out);
+bool entries_genz_product_peak_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_product_peak_y53(int prec, int d, KernelEntry* out);
+bool entries_genz_corner_peak_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_corner_peak_y53(int prec, int d, KernelEntry* out);
+bool entries_genz_oscillatory_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_oscillatory_y53(int prec, int d, KernelEntry* out);
+bool entries_dgauss_y24(int prec, int d, KernelEntry* out);
+bool entries_dgauss_y53(int prec, int d, KernelEntry* out);
+bool entries_rambo_y24(int prec, int d, KernelEntry* out);
+bool entries_rambo_y53(int prec, int d, KernelEntry* out);
 
 // Arguments of the per-sample dump kernel.
 struct DumpArgs {
@@ -43,6 +53,8 @@ struct DumpArgs {
 extern "C" {
 cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s);
+cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
+cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s);
 cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,
                              cudaStream_t s);
 }

@@ -6,8 +6,8 @@
 //
 // Template parameters: T (double or float: map and integrand precision),
 // DM (compile-time bound on ndim), F (integrand), ACC (0: FP64 sums,
-// 1: FP32 point values into FP64 sums, 2: compensated FP32 sums with FP64
-// flushes).
+// 1: FP32 point values into FP64 sums, 2: compensated FP32 sums), YB (24 or
+// 53 random bits per axis).
 #pragma once
 
 #include <type_traits>
@@ -27,12 +27,10 @@ template <> struct AccTraits<2> { using H = float; };
 template <int ACC> struct Run {
   double s = 0.0;
   __device__ __forceinline__ void add(double v) { s += v; }
-  __device__ __forceinline__ void add(float v) { s += (double)v; }
   __device__ __forceinline__ double value() const { return s; }
   __device__ __forceinline__ void shfl_merge(int off, int width) {
     s += __shfl_xor_sync(0xffffffffu, s, off, width);
   }
-  __device__ __forceinline__ void reset() { s = 0.0; }
 };
 template <> struct Run<2> {
   fpair p{0.f, 0.f};
@@ -44,17 +42,82 @@ template <> struct Run<2> {
     q.lo = __shfl_xor_sync(0xffffffffu, p.lo, off, width);
     comp_merge(p, q);
   }
-  __device__ __forceinline__ void reset() { p.hi = p.lo = 0.f; }
 };
+
+// FP32 in-bin fraction from the top 23 of 24 fraction bits v: the float
+// 1 + (v >> 1) 2^-23 minus one, exact (two instructions, no conversion unit).
+__device__ __forceinline__ float frac23(uint32_t v24) {
+  return __uint_as_float(0x3F800000u | (v24 >> 1)) - 1.0f;
+}
+
+// Grid bin k and position in the bin (as a fraction) of axis a from its
+// random bits m (YB bits) and hypercube digit c: g y = c + m / 2^YB,
+// k = floor(y N), frac = y N - k, in integer arithmetic.  The FP32 kernels
+// keep the top 23 bits of the fraction (an error below 2^-24 of a bin).
+template <typename T, int YB, bool SPEC>
+__device__ __forceinline__ void bin_frac(const SampleArgs& A, uint64_t m, int c, int& k, T& fr) {
+  const uint32_t N = (uint32_t)A.N;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  if (SPEC) {  // 24 bits, power-of-two divisions, g N <= 256 (checked on the host)
+    const uint32_t t = (((uint32_t)c << 24) | (uint32_t)m) * N;
+    const int sh = 24 + A.g_log2;
+    k = (int)(t >> sh);
+    const uint32_t r = t & ((1u << sh) - 1u);
+    if (F32)
+      fr = T(frac23(r >> A.g_log2));
+    else
+      fr = T((double)r * A.inv_gb_d);
+    return;
+  }
+  if (YB == 24 && A.t32) {
+    const uint32_t t = (((uint32_t)c << 24) | (uint32_t)m) * N;  // g 2^24 y N < 2^32
+    uint32_t r;
+    if (A.g_pow2) {
+      const int sh = 24 + A.g_log2;
+      k = (int)(t >> sh);
+      r = t & ((1u << sh) - 1u);
+      if (F32) {
+        fr = T(frac23(r >> A.g_log2));
+        return;
+      }
+    } else {
+      k = (int)((t >> 24) / (uint32_t)A.g);
+      r = t - (uint32_t)k * ((uint32_t)A.g << 24);
+    }
+    if (F32)
+      fr = T((float)r * A.inv_gb_f);
+    else
+      fr = T((double)r * A.inv_gb_d);
+    return;
+  }
+  const uint64_t t = (((uint64_t)c << YB) | m) * (uint64_t)N;
+  uint64_t r;
+  if (A.g_pow2) {
+    const int sh = YB + A.g_log2;
+    k = (int)(t >> sh);
+    r = t & ((1ull << sh) - 1ull);
+    if (F32) {
+      fr = T(frac23((uint32_t)(r >> (sh - 24))));
+      return;
+    }
+  } else {
+    k = (int)((uint32_t)(t >> YB) / (uint32_t)A.g);
+    r = t - (((uint64_t)k * (uint64_t)A.g) << YB);
+  }
+  if (F32)
+    fr = T((float)r * A.inv_gb_f);
+  else
+    fr = T((double)r * A.inv_gb_d);
+}
 
 // Point generation for one sample: bins kb[a], point x[a] and the Jacobian.
 // `cd` holds the hypercube digits c_a (zero without stratification).
-template <typename T, int DM>
+template <typename T, int DM, int YB, bool SPEC = false>
 __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32_t s,
                                         const int (&cd)[DM],
                                         const typename Vec2<T>::type* tab,
                                         T (&x)[DM], int (&kb)[DM], uint32_t* words_out) {
-  const int d = A.d, N = A.N;
+  const int d = SPEC ? DM : A.d, N = A.N;
   const T Nf = T(N);
   T J = T(1);
   uint4 w4 = make_uint4(0, 0, 0, 0);
@@ -62,13 +125,11 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   for (int a = 0; a < DM; ++a) {
     if (a < d) {
       uint64_t m;
-      int b;
-      if (A.ybits == 24) {
+      if (YB == 24) {
         if ((a & 3) == 0) w4 = philox4x32_10(make_uint4(s, (uint32_t)(a >> 2), it, A.instance), A.key0, A.key1);
         const uint32_t u = pick(w4, a & 3);
         if (words_out) words_out[a] = u;
         m = u >> 8;
-        b = 24;
       } else {
         if (((2 * a) & 3) == 0)
           w4 = philox4x32_10(make_uint4(s, (uint32_t)((2 * a) >> 2), it, A.instance), A.key0, A.key1);
@@ -78,34 +139,10 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
           words_out[2 * a + 1] = ul;
         }
         m = ((uint64_t)(uh >> 5) << 26) | (uint64_t)(ul >> 6);
-        b = 53;
       }
       int k;
       T fr;
-      if (!A.strat) {
-        if (b == 24) {
-          const uint32_t t = (uint32_t)m * (uint32_t)N;  // < 2^32 for N <= 256
-          k = (int)(t >> 24);
-          fr = T(t & 0xFFFFFFu) * T(1.0 / 16777216.0);
-        } else {
-          const uint64_t t = m * (uint64_t)N;
-          k = (int)(t >> 53);
-          fr = T(t & ((1ull << 53) - 1)) * T(1.0 / 9007199254740992.0);
-        }
-      } else {
-        const uint64_t Y = ((uint64_t)cd[a] << b) | m;
-        const uint64_t t = Y * (uint64_t)N;
-        const uint32_t top = (uint32_t)(t >> b);  // floor(g y N) < g N
-        if (A.g_pow2) {
-          k = (int)(top >> A.g_log2);
-          const uint64_t r = t & ((1ull << (b + A.g_log2)) - 1);
-          fr = T(r) * T(1.0 / (double)(1ull << (b + A.g_log2)) );
-        } else {
-          k = (int)(top / (uint32_t)A.g);
-          const uint64_t r = t - ((uint64_t)k * (uint64_t)A.g << b);
-          fr = T(r) / T((double)A.g * (double)(1ull << b));
-        }
-      }
+      bin_frac<T, YB, SPEC>(A, m, cd[a], k, fr);
       const typename Vec2<T>::type e = tab[a * N + k];
       x[a] = vfma(fr, e.y, e.x);
       J *= Nf * e.y;
@@ -115,53 +152,129 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   return J;
 }
 
-template <typename T, int DM, template <typename, int> class F, int ACC>
+// Shared memory layout of k_sample (byte offsets): grid table, integrand
+// constants, bucket counters [d N] (int), buckets [cap][d N] (H), the
+// overflow histogram [2][d][N] (H, atomics), the CTA histogram [2][d][N]
+// (H), and for ACC 2 its compensated pairs [2][d][N].
+template <typename T, int ACC>
+struct SmemLayout {
+  using H = typename AccTraits<ACC>::H;
+  static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
+  static __host__ __device__ size_t params(int dN) { return (size_t)dN * sizeof(typename Vec2<T>::type); }
+  static __host__ __device__ size_t cnt(int dN) { return a16(params(dN) + kNumDerived * sizeof(T)); }
+  static __host__ __device__ size_t bucket(int dN) { return a16(cnt(dN) + (size_t)dN * sizeof(int)); }
+  static __host__ __device__ size_t ovf(int dN, int cap) { return a16(bucket(dN) + (size_t)cap * dN * sizeof(H)); }
+  static __host__ __device__ size_t cta(int dN, int cap) { return a16(ovf(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
+  static __host__ __device__ size_t comp(int dN, int cap) { return a16(cta(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
+  static __host__ __device__ size_t total(int dN, int cap) {
+    return comp(dN, cap) + (ACC == 2 ? 2 * (size_t)dN * sizeof(fpair) : 0);
+  }
+};
+
+// Tiles between compensated folds of the CTA histogram (ACC 2): the plain
+// FP32 cells then add at most this many bucket sums.
+constexpr int kFoldTiles = 8;
+
+// Warp all-reduce of a compensated pair (fixed xor order).
+__device__ __forceinline__ fpair warp_sum(fpair p) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fpair q;
+    q.hi = __shfl_xor_sync(0xffffffffu, p.hi, off);
+    q.lo = __shfl_xor_sync(0xffffffffu, p.lo, off);
+    comp_merge(p, q);
+  }
+  return p;
+}
+
+template <typename T, int DM, template <typename, int> class F, int ACC, int YB, bool SPEC>
 __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   using H = typename AccTraits<ACC>::H;
   using T2 = typename Vec2<T>::type;
+  using L = SmemLayout<T, ACC>;
+  constexpr bool COMP = ACC == 2;  // FP32 throughout, no FP64 in the loop
   if (A.st->done) return;  // the ACC test stopped this call (device-side)
   const uint32_t it = A.it_override >= 0 ? (uint32_t)A.it_override : A.st->it;
-  const int d = A.d, N = A.N, dN = d * N;
+  // SPEC: d equals the compile-time bound DM, 24-bit words and power-of-two
+  // hypercube divisions with g N <= 256: every per-axis guard folds away.
+  const int d = SPEC ? DM : A.d, N = A.N, dN = d * N, cap = A.cap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
-  T* P = reinterpret_cast<T*>(tab + dN);
-  double* hd = reinterpret_cast<double*>(
-      (reinterpret_cast<uintptr_t>(P + kNumDerived) + 15) & ~uintptr_t(15));  // FP64 histogram [2][d][N]
-  H* hs = reinterpret_cast<H*>(ACC == 2 ? (void*)(hd + 2 * dN) : (void*)hd);  // histogram atomics target
+  T* P = reinterpret_cast<T*>(smem + L::params(dN));
+  int* cnt = reinterpret_cast<int*>(smem + L::cnt(dN));
+  H* bucket = reinterpret_cast<H*>(smem + L::bucket(dN));   // [cap][d N]
+  H* ovf = reinterpret_cast<H*>(smem + L::ovf(dN, cap));     // [2][d N]
+  H* cta = reinterpret_cast<H*>(smem + L::cta(dN, cap));     // [2][d N]
+  fpair* cmp = reinterpret_cast<fpair*>(smem + L::comp(dN, cap));  // ACC 2: [2][d N]
 
-  const int tid = threadIdx.x;
   // Coalesced, vectorised grid-table load (one 8- or 16-byte cell per bin).
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
+  for (int i = tid; i < dN; i += blockDim.x) cnt[i] = 0;
   for (int i = tid; i < 2 * dN; i += blockDim.x) {
-    hd[i] = 0.0;
-    if (ACC == 2) hs[i] = H(0);
+    ovf[i] = H(0);
+    cta[i] = H(0);
+    if (COMP) cmp[i] = fpair{0.f, 0.f};
   }
   __syncthreads();
 
-  Run<ACC> sw, sw2;      // point totals
-  double sI = 0.0, sV = 0.0;  // stratified: sum of cube means, cube-mean variances
   int nonfinite = 0;
   int cd[DM];
 #pragma unroll
   for (int a = 0; a < DM; ++a) cd[a] = 0;
 
-  auto accumulate_bins = [&](const int (&kb)[DM], H w) {
-    const H w2 = w * w;
+  // Bucketed tile histogram (shared-memory float atomics are compare-and-
+  // swap loops on this GPU, 32-bit integer atomics are native): a point
+  // claims a slot of its (axis, bin) bucket with one integer atomicAdd and
+  // stores w there; full buckets spill into the overflow histogram.
+  auto scatter = [&](const int (&kb)[DM], H w) {
 #pragma unroll
     for (int a = 0; a < DM; ++a)
       if (a < d) {
-        atomicAdd(&hs[a * N + kb[a]], (H)w);
-        atomicAdd(&hs[dN + a * N + kb[a]], (H)w2);
+        const int cell = a * N + kb[a];
+        const int pos = atomicAdd(&cnt[cell], 1);
+        if (pos < cap) {
+          bucket[pos * dN + cell] = w;
+        } else {
+          atomicAdd(&ovf[cell], w);
+          atomicAdd(&ovf[dN + cell], w * w);
+        }
       }
   };
-  auto flush = [&]() {  // compensated mode: FP32 histogram -> FP64 histogram
+  // End of a tile: one thread per cell sums its bucket (w and w^2) into the
+  // CTA histogram; the bucket layout [slot][cell] keeps this conflict-free.
+  // ACC 2 folds the FP32 cells into compensated pairs every kFoldTiles.
+  int tile = 0;
+  auto gather = [&]() {
     __syncthreads();
-    for (int i = tid; i < 2 * dN; i += blockDim.x) {
-      hd[i] += (double)hs[i];
-      hs[i] = H(0);
+    const bool fold = COMP && (++tile % kFoldTiles == 0);
+    for (int cell = tid; cell < dN; cell += blockDim.x) {
+      const int n = min(cnt[cell], cap);
+      H s1 = H(0), s2 = H(0);
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        const H v0 = bucket[j * dN + cell], v1 = bucket[(j + 1) * dN + cell];
+        const H v2 = bucket[(j + 2) * dN + cell], v3 = bucket[(j + 3) * dN + cell];
+        s1 += (v0 + v1) + (v2 + v3);
+        s2 += (v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3);
+      }
+      for (; j < n; ++j) {
+        const H v = bucket[j * dN + cell];
+        s1 += v;
+        s2 += v * v;
+      }
+      H c1 = cta[cell] + s1, c2 = cta[dN + cell] + s2;
+      if (fold) {
+        comp_add(cmp[cell], (float)c1);
+        comp_add(cmp[dN + cell], (float)c2);
+        c1 = c2 = H(0);
+      }
+      cta[cell] = c1;
+      cta[dN + cell] = c2;
+      cnt[cell] = 0;
     }
     __syncthreads();
   };
@@ -169,7 +282,7 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   // (squares are then formed in H: FP64 unless ACC == 2).
   auto eval_point = [&](uint32_t s, int (&kb)[DM]) -> H {
     T x[DM];
-    const T J = make_point<T, DM>(A, it, s, cd, tab, x, kb, nullptr);
+    const T J = make_point<T, DM, YB, SPEC>(A, it, s, cd, tab, x, kb, nullptr);
     const T f = F<T, DM>::eval(x, d, P);
     T w = f * J;
     if (!vfinite(w)) {
@@ -179,122 +292,191 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
     return (H)w;
   };
 
+  // Totals: sum w, sum w^2, sum of cube means, sum of cube-mean variances;
+  // FP64 (ACC 0/1) or compensated FP32 pairs (ACC 2).
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  fpair tp[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (!A.strat) {
+    Run<ACC> sw, sw2;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x;
     const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
-    for (uint64_t r = 0; r < rounds; ++r) {
-      const uint64_t s = first + tid + r * stride;
+    uint64_t s = first + tid;
+    for (uint64_t r = 0; r < rounds; ++r, s += stride) {
       if (s < A.ncall) {
         int kb[DM];
         const H w = eval_point((uint32_t)s, kb);
         sw.add(w);
         sw2.add(w * w);
-        accumulate_bins(kb, w);
+        scatter(kb, w);
       }
-      if (ACC == 2 && ((r + 1) % (uint64_t)A.flush_rounds == 0)) flush();
+      gather();
+    }
+    if constexpr (COMP) {
+      tp[0] = sw.p;
+      tp[1] = sw2.p;
+    } else {
+      t[0] = sw.value();
+      t[1] = sw2.value();
     }
   } else {
-    // Groups of L lanes share a hypercube; lane j of a group takes the
-    // cube's points j, j + L, ...; the group then reduces its sums with a
-    // fixed xor-butterfly (deterministic).
-    const int L = A.lanes;
-    const int lane = tid & 31;
-    const int gl = lane & (L - 1);
-    const uint64_t groups_per_cta = blockDim.x / L;
-    const uint64_t gstride = (uint64_t)gridDim.x * groups_per_cta;
-    const uint64_t gfirst = (uint64_t)blockIdx.x * groups_per_cta;
-    const uint64_t rounds = gfirst < A.ncubes ? (A.ncubes - gfirst + gstride - 1) / gstride : 0;
-    for (uint64_t r = 0; r < rounds; ++r) {
-      const uint64_t c = gfirst + tid / L + r * gstride;
-      const bool live = c < A.ncubes;  // uniform within a group
-      Run<ACC> c1, c2;
+    // Groups of Lw lanes share a hypercube; lane j of a group takes the
+    // cube's points j, j + Lw, ... in lock-step with the rest of the CTA
+    // (one tile per step); the group then reduces its sums with a fixed
+    // xor-butterfly (deterministic).  Group i takes cube
+    // (i * cube_mul) mod ncubes, so that the groups of a CTA sit in
+    // unrelated cubes and spread over the bins.
+    const int Lw = A.lanes;
+    const int gl = tid & (Lw - 1);
+    const uint32_t groups_per_cta = blockDim.x / Lw;
+    const uint32_t gstride = gridDim.x * groups_per_cta;
+    const uint32_t gfirst = blockIdx.x * groups_per_cta;
+    const uint32_t rounds = gfirst < A.ncubes ? (A.ncubes - gfirst + gstride - 1) / gstride : 0;
+    const uint32_t cmask = A.ncubes - 1u;
+    const uint32_t per_lane = (A.nc + Lw - 1) / Lw;
+    uint32_t gi = gfirst + tid / Lw;
+    for (uint32_t r = 0; r < rounds; ++r, gi += gstride) {
+      const bool live = gi < A.ncubes;  // uniform within a group
+      const uint32_t c = A.cube_mul == 1u ? gi : (gi * A.cube_mul) & cmask;
       if (live) {
-        uint64_t rest = c;
+        uint32_t rest = c;
 #pragma unroll
         for (int a = 0; a < DM; ++a)
           if (a < d) {
             if (A.g_pow2) {
-              cd[a] = (int)(rest & (uint64_t)(A.g - 1));
+              cd[a] = (int)(rest & (uint32_t)(A.g - 1));
               rest >>= A.g_log2;
             } else {
-              cd[a] = (int)(rest % (uint64_t)A.g);
-              rest /= (uint64_t)A.g;
+              cd[a] = (int)(rest % (uint32_t)A.g);
+              rest /= (uint32_t)A.g;
             }
           }
-        const uint64_t s0 = c * A.nc;
-        for (uint64_t j = gl; j < A.nc; j += L) {
+      }
+      const uint32_t s0 = c * A.nc;
+      // a lane's chain of points in one cube is short: plain sums in H,
+      // compensated merges across the group
+      H p1 = H(0), p2 = H(0);
+      for (uint32_t i = 0; i < per_lane; ++i) {
+        const uint32_t j = gl + i * Lw;
+        if (live && j < A.nc) {
           int kb[DM];
-          const H w = eval_point((uint32_t)(s0 + j), kb);
-          c1.add(w);
-          c2.add(w * w);
-          accumulate_bins(kb, w);
+          const H w = eval_point(s0 + j, kb);
+          p1 += w;
+          p2 += w * w;
+          scatter(kb, w);
+        }
+        gather();
+      }
+      if constexpr (COMP) {
+        fpair c1{p1, 0.f}, c2{p2, 0.f};
+        for (int off = Lw >> 1; off > 0; off >>= 1) {
+          fpair o1, o2;
+          o1.hi = __shfl_xor_sync(0xffffffffu, c1.hi, off, Lw);
+          o1.lo = __shfl_xor_sync(0xffffffffu, c1.lo, off, Lw);
+          o2.hi = __shfl_xor_sync(0xffffffffu, c2.hi, off, Lw);
+          o2.lo = __shfl_xor_sync(0xffffffffu, c2.lo, off, Lw);
+          comp_merge(c1, o1);
+          comp_merge(c2, o2);
+        }
+        if (live && gl == 0) {
+          // cube mean m = C1 / nc and variance (C2 / nc - m^2) / (nc - 1),
+          // in FP32 with the square formed exactly (FMA) and the pairs kept
+          const float inv = (float)A.inv_nc, inv1 = (float)A.inv_nc1;
+          const float mh = c1.hi * inv, ml = c1.lo * inv;
+          const float sq = mh * mh;
+          const float sqe = fmaf(mh, mh, -sq) + 2.0f * mh * ml;
+          const float e2h = c2.hi * inv, e2l = c2.lo * inv;
+          float v = ((e2h - sq) + (e2l - sqe)) * inv1;
+          if (!(v > 0.f)) v = 0.f;
+          comp_merge(tp[0], c1);
+          comp_merge(tp[1], c2);
+          comp_add(tp[2], mh);
+          comp_add(tp[2], ml);
+          comp_add(tp[3], v);
+          if (A.cubes)
+            reinterpret_cast<float4*>(A.cubes)[c] = make_float4(c1.hi, c1.lo, c2.hi, c2.lo);
+        }
+      } else {
+        double c1 = p1, c2 = p2;
+        for (int off = Lw >> 1; off > 0; off >>= 1) {
+          c1 += __shfl_xor_sync(0xffffffffu, c1, off, Lw);
+          c2 += __shfl_xor_sync(0xffffffffu, c2, off, Lw);
+        }
+        if (live && gl == 0) {
+          const double m = c1 * A.inv_nc;
+          double v = (c2 * A.inv_nc - m * m) * A.inv_nc1;
+          if (v < 0.0) v = 0.0;
+          t[0] += c1;
+          t[1] += c2;
+          t[2] += m;
+          t[3] += v;
+          if (A.cubes) {
+            reinterpret_cast<double*>(A.cubes)[2 * (size_t)c] = c1;
+            reinterpret_cast<double*>(A.cubes)[2 * (size_t)c + 1] = c2;
+          }
         }
       }
-      for (int off = L >> 1; off > 0; off >>= 1) {
-        c1.shfl_merge(off, L);
-        c2.shfl_merge(off, L);
-      }
-      if (live && gl == 0) {
-        const double C1 = c1.value(), C2 = c2.value();
-        const double nc = (double)A.nc;
-        const double m = C1 / nc;
-        double v = (C2 / nc - m * m) / (nc - 1.0);
-        if (v < 0.0) v = 0.0;
-        sI += m;
-        sV += v;
-        sw.add(C1);
-        sw2.add(C2);
-        if (A.cubes) {
-          A.cubes[2 * c] = C1;
-          A.cubes[2 * c + 1] = C2;
-        }
-      }
-      if (ACC == 2 && ((r + 1) % (uint64_t)A.flush_rounds == 0)) flush();
     }
   }
-  if (ACC == 2) flush();
   __syncthreads();
 
-  // Partial row of this CTA: histograms, then totals (fixed-order reduction).
+  // Partial row of this CTA: histogram cells (FP64, or compensated FP32
+  // pairs) including the overflow cells, then the totals.
   const int np = A.nparts, row = blockIdx.x;
-  for (int i = tid; i < 2 * dN; i += blockDim.x) A.part_bins[(size_t)i * np + row] = hd[i];
+  for (int i = tid; i < 2 * dN; i += blockDim.x) {
+    if constexpr (COMP) {
+      fpair p = cmp[i];
+      comp_add(p, (float)cta[i]);
+      comp_add(p, (float)ovf[i]);
+      reinterpret_cast<float2*>(A.part_bins)[(size_t)i * np + row] = make_float2(p.hi, p.lo);
+    } else {
+      reinterpret_cast<double*>(A.part_bins)[(size_t)i * np + row] = (double)cta[i] + (double)ovf[i];
+    }
+  }
 
-  double t[5] = {sw.value(), sw2.value(), sI, sV, (double)nonfinite};
+  __shared__ double wsum[8][5];
+  __shared__ fpair wpair[8][4];
+  if constexpr (COMP) {
 #pragma unroll
-  for (int q = 0; q < 5; ++q)
+    for (int q = 0; q < 4; ++q) {
+      const fpair v = warp_sum(tp[q]);
+      if (lane == 0) wpair[warp][q] = v;
+    }
+  } else {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
-  __shared__ double wsum[32][5];
-  const int warp = tid >> 5, nw = blockDim.x >> 5;
-  if ((tid & 31) == 0)
+    for (int q = 0; q < 4; ++q) {
+      double v = t[q];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) wsum[warp][q] = t[q];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) wsum[warp][q] = v;
+    }
+  }
+  int nf = nonfinite;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, off);
+  if (lane == 0) wsum[warp][4] = (double)nf;
   __syncthreads();
   if (tid < 5) {
     double acc = 0.0;
-    for (int w = 0; w < nw; ++w) acc += wsum[w][tid];
+    if (COMP && tid < 4) {
+      fpair p{0.f, 0.f};
+      for (int w = 0; w < nw; ++w) comp_merge(p, wpair[w][tid]);
+      acc = comp_value(p);
+    } else {
+      for (int w = 0; w < nw; ++w) acc += wsum[w][tid];
+    }
     A.part_tot[(size_t)tid * np + row] = acc;
   }
 }
 
-// Shared memory of k_sample for a given shape.
 template <typename T, int ACC>
-inline size_t sample_smem_bytes(int d, int N) {
-  size_t b = (size_t)d * N * sizeof(typename Vec2<T>::type) + kNumDerived * sizeof(T);
-  b = (b + 15) & ~size_t(15);
-  b += 2 * (size_t)d * N * sizeof(double);
-  if (ACC == 2) b += 2 * (size_t)d * N * sizeof(float);
-  return b + 16;
+inline size_t sample_smem_bytes(int d, int N, int cap) {
+  return SmemLayout<T, ACC>::total(d * N, cap);
 }
-
-}  // namespace gv
-
-namespace gv {
 
 // Steps 2-3 for a list of sample indices (parity checks and debugging):
 // the Philox words, bins, point, Jacobian and integrand value of each.
-template <typename T, int DM, template <typename, int> class F>
+template <typename T, int DM, template <typename, int> class F, int YB>
 __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
   __shared__ T P[kNumDerived];
   for (int i = threadIdx.x; i < kNumDerived; i += blockDim.x) P[i] = (T)D.S.dparams[i];
@@ -317,10 +499,10 @@ __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
   T x[DM];
   int kb[DM];
   uint32_t wl[2 * DM];
-  const T J = make_point<T, DM>(A, it, (uint32_t)s, cd,
-                                reinterpret_cast<const typename Vec2<T>::type*>(A.tab), x, kb, wl);
+  const T J = make_point<T, DM, YB>(A, it, (uint32_t)s, cd,
+                                    reinterpret_cast<const typename Vec2<T>::type*>(A.tab), x, kb, wl);
   const T f = F<T, DM>::eval(x, A.d, P);
-  const int W = A.ybits == 24 ? A.d : 2 * A.d;
+  const int W = YB == 24 ? A.d : 2 * A.d;
   if (D.words)
     for (int j = 0; j < W; ++j) D.words[i * W + j] = wl[j];
 #pragma unroll
@@ -333,33 +515,47 @@ __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
   if (D.f) D.f[i] = (double)f;
 }
 
-template <typename T, int DM, template <typename, int> class F, int ACC>
+template <typename T, int DM, template <typename, int> class F, int ACC, int YB>
+inline const void* spec_kernel() {
+  if constexpr (YB == 24 && ACC != 1)
+    return (const void*)&k_sample<T, DM, F, ACC, 24, true>;
+  else
+    return nullptr;
+}
+
+template <typename T, int DM, template <typename, int> class F, int ACC, int YB>
 inline KernelEntry make_entry() {
   KernelEntry e;
-  e.sample = (const void*)&k_sample<T, DM, F, ACC>;
-  e.dump = (const void*)&k_dump<T, DM, F>;
+  e.sample = (const void*)&k_sample<T, DM, F, ACC, YB, false>;
+  e.sample_spec = spec_kernel<T, DM, F, ACC, YB>();
+  e.dump = (const void*)&k_dump<T, DM, F, YB>;
   e.smem = &sample_smem_bytes<T, ACC>;
   e.dm = DM;
   return e;
 }
 
-template <template <typename, int> class F, int DM>
-inline bool pick_precision(int prec, KernelEntry* out) {
+template <template <typename, int> class F, int DM, int YB>
+inline bool pick_precision_yb(int prec, KernelEntry* out) {
   switch (prec) {
-    case VG_FP64: *out = make_entry<double, DM, F, 0>(); return true;
-    case VG_FP32_ACC64: *out = make_entry<float, DM, F, 1>(); return true;
-    case VG_FP32_ACCCOMP: *out = make_entry<float, DM, F, 2>(); return true;
+    case VG_FP64: *out = make_entry<double, DM, F, 0, YB>(); return true;
+    case VG_FP32_ACC64: *out = make_entry<float, DM, F, 1, YB>(); return true;
+    case VG_FP32_ACCCOMP: *out = make_entry<float, DM, F, 2, YB>(); return true;
     default: return false;
   }
 }
 
+template <template <typename, int> class F, int DM>
+inline bool pick_precision(int prec, int ybits, KernelEntry* out) {
+  return ybits == 24 ? pick_precision_yb<F, DM, 24>(prec, out) : pick_precision_yb<F, DM, 53>(prec, out);
+}
+
 // Smallest instantiated bound from {4, 8, 16, 32} that covers d.
 template <template <typename, int> class F>
-inline bool pick_pow2_bound(int prec, int d, KernelEntry* out) {
-  if (d <= 4) return pick_precision<F, 4>(prec, out);
-  if (d <= 8) return pick_precision<F, 8>(prec, out);
-  if (d <= 16) return pick_precision<F, 16>(prec, out);
-  if (d <= 32) return pick_precision<F, 32>(prec, out);
+inline bool pick_pow2_bound(int prec, int ybits, int d, KernelEntry* out) {
+  if (d <= 4) return pick_precision<F, 4>(prec, ybits, out);
+  if (d <= 8) return pick_precision<F, 8>(prec, ybits, out);
+  if (d <= 16) return pick_precision<F, 16>(prec, ybits, out);
+  if (d <= 32) return pick_precision<F, 32>(prec, ybits, out);
   return false;
 }
 

@@ -64,6 +64,7 @@ _SIGS = {
     "vegas_destroy": (None, [_P]),
     "vegas_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result)]),
     "vegas_reset_results": (ctypes.c_int, [_P]),
+    "vegas_reset_grid": (ctypes.c_int, [_P]),
     "bases_integrate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_double, ctypes.POINTER(Result),
                                        ctypes.POINTER(Result)]),
@@ -83,6 +84,8 @@ _SIGS = {
     "vegas_set_launch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "vegas_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
+    "vegas_microbench": (ctypes.c_int, [ctypes.c_int, _DP]),
     "vegas_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -179,11 +182,17 @@ def vegas_reset_results(ctx: Context):
     _check(lib().vegas_reset_results(ctx.handle), ctx.handle)
 
 
-def bases_integrate(ctx: Context, itmx1: int, acc1: float, itmx2: int, acc2: float):
+def vegas_reset_grid(ctx: Context):
+    _check(lib().vegas_reset_grid(ctx.handle), ctx.handle)
+
+
+def bases_integrate(ctx: Context, itmx1: int, acc1: float, itmx2: int, acc2: float,
+                    result: bool = True):
     out, ph1 = Result(), Result()
     _check(lib().bases_integrate(ctx.handle, int(itmx1), float(acc1), int(itmx2), float(acc2),
-                                 ctypes.byref(out), ctypes.byref(ph1)), ctx.handle)
-    return out.as_dict(), ph1.as_dict()
+                                 ctypes.byref(out) if result else None,
+                                 ctypes.byref(ph1) if result else None), ctx.handle)
+    return (out.as_dict(), ph1.as_dict()) if result else None
 
 
 def vegas_get_grid(ctx: Context, bin_sums: bool = False):
@@ -270,6 +279,27 @@ def vegas_get_launch(ctx: Context):
     t, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().vegas_get_launch(ctx.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(o)), ctx.handle)
     return dict(threads=t.value, ctas=c.value, occupancy=o.value)
+
+
+def vegas_profile_pass(ctx: Context, n_pass: int = 10):
+    """Mean milliseconds per launch of (sampling, reduction, finalisation)."""
+    ms = np.zeros(3)
+    _check(lib().vegas_profile_pass(ctx.handle, int(n_pass), _dp(ms)), ctx.handle)
+    return dict(sample=ms[0], reduce=ms[1], finalize=ms[2])
+
+
+MICROBENCH_OPS = {0: "ffma", 1: "imad_wide", 2: "dfma", 3: "mufu_ex2", 4: "i2f", 5: "philox_block",
+                  6: "smem_atomic_f32_cta", 7: "smem_atomic_f32_warp", 8: "smem_atomic_i32",
+                  9: "smem_atomic_f64", 10: "philox_block_wide", 11: "shfl",
+                  12: "owner_bin_update", 13: "smem_atomic_u64_cta", 14: "smem_atomic_u64_warp",
+                  15: "smem_atomic_i32_warp"}
+
+
+def vegas_microbench(op: int) -> float:
+    """Thread-operations per second of one instruction class (see the header)."""
+    r = ctypes.c_double()
+    _check(lib().vegas_microbench(int(op), ctypes.byref(r)))
+    return r.value
 
 
 def vegas_last_error(ctx: Context | None = None) -> str:

@@ -171,3 +171,58 @@ def test_acc_stops_early_on_device(gv):
         it = gv.vegas_get_iteration(ctx)
     assert r["stopped"] == 1 and r["iters_done"] < 50 and it == r["iters_done"]
     assert r["sigma"] < 1e-3 * abs(r["I"])
+
+
+@pytest.mark.parametrize("N", [2, 31, 33, 64, 65, 100, 256])
+@pytest.mark.parametrize("precision", [0, 2])
+def test_bin_counts_across_histogram_paths(gv, orc, N, precision):
+    """nbins <= 64 uses warp bin ownership, larger counts the atomic path; both
+    must give the oracle's per-bin sums (ragged NCALL, two iterations with a
+    refined grid in between)."""
+    d, ncall = 3, 3 * 4096 + 17
+    params = wl.genz_gaussian_params(d, a=6.0, u=0.4)
+    ctx, cfg, fn = _pair(gv, orc, wl.GENZ_GAUSSIAN, d, params, N=N, ncall=ncall, precision=precision,
+                         ybits=24)
+    e = orc.uniform_grid(d, N)
+    with ctx:
+        gv.vegas_iterate(ctx, 1, refine=True)
+        I, var = gv.vegas_eval(ctx, 1)
+        edges, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o0 = orc.iteration(cfg, fn, e, 0)
+    e1 = orc.refine(o0["S2"], e)
+    tol = 1e-12 if precision == 0 else 1e-5
+    np.testing.assert_allclose(edges, e1, rtol=0, atol=1e-12 if precision == 0 else 1e-6)
+    o1 = orc.iteration(cfg, fn, edges, 1)  # oracle on the GPU's grid: same points
+    p = orc.sample_batch(cfg, edges, 1, np.arange(ncall))
+    absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    assert _cond_close(bins[0], o1["S1"], absw.sum(), tol)
+    assert _cond_close(bins[1], o1["S2"], (absw ** 2).sum(), tol)
+    assert abs(I - o1["I"]) <= tol * absw.mean()
+
+
+@pytest.mark.parametrize("ncall", [2, 3, 31, 33, 255, 257, 100003])
+def test_tiny_and_ragged_ncall(gv, orc, ncall):
+    d = 2
+    params = np.array([3.0, 5.0, 0.3, 0.6])
+    ctx, cfg, fn = _pair(gv, orc, wl.GENZ_PRODUCT_PEAK, d, params, ncall=ncall, precision=0)
+    with ctx:
+        I, var = gv.vegas_eval(ctx, 0)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 0)
+    assert I == pytest.approx(o["I"], rel=1e-12)
+    assert var == pytest.approx(o["var"], rel=1e-9, abs=1e-300)
+    np.testing.assert_allclose(bins[0], o["S1"], rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("d,precision", [(1, 0), (1, 2), (32, 0), (32, 2), (17, 2)])
+def test_dimension_extremes(gv, orc, d, precision):
+    params = np.concatenate([np.full(d, 0.3), np.full(d, 0.5)])
+    ctx, cfg, fn = _pair(gv, orc, wl.GENZ_PRODUCT_PEAK, d, params, ncall=20000, precision=precision,
+                         ybits=24)
+    with ctx:
+        I, var = gv.vegas_eval(ctx, 4)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 4)
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert I == pytest.approx(o["I"], rel=tol)
+    np.testing.assert_allclose(bins[0], o["S1"], rtol=tol, atol=tol * np.abs(o["S1"]).max())
