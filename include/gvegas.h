@@ -260,6 +260,29 @@ vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
  * Launches its own kernels on the legacy default stream and synchronises. */
 vegas_status vegas_microbench(int op, double* rate);
 
+/* One evaluation pass that allocates no device memory (the paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc, such as
+ * code living inside another runtime's fixed memory pool or a
+ * latency-critical loop where an allocation, which may synchronise the
+ * device or fail under fragmentation, is not allowed after start-up).
+ * Same pass as vegas_eval, without a context: `config` and `integrand` as
+ * for vegas_create (config->stream orders the work; NULL means the legacy
+ * default stream), `edges` a DEVICE array [ndim][nbins+1] holding the grid,
+ * `it` the Philox iteration index (< 2^31), `out` a DEVICE array of
+ * 2 ndim nbins + 5 doubles receiving the per-bin sums (sum w, then sum w^2,
+ * as vegas_get_grid) followed by I, its variance, sum w, sum w^2 and the
+ * count of non-finite weights.  Asynchronous: `out` is ready when the stream
+ * reaches it.  Every intermediate lives in one static 8 MiB device array of
+ * the library (held by every GPU that loads it until the process exits);
+ * shapes whose partial sums do not fit in it (ndim nbins beyond about
+ * 60 000 cells) are rejected with VEGAS_EINVAL.  The first call on a device
+ * looks up that array's device address, so make it before any stream
+ * capture.  All calls share the array and each call overwrites it: calls
+ * that overlap on the GPU (other streams, other host threads) race and give
+ * wrong results. */
+vegas_status vegas_eval_noalloc(const vegas_config* config, const vegas_integrand* integrand,
+                                const double* edges, uint32_t it, double* out);
+
 /* Message of the last failure on ctx (or of the calling thread when ctx is
  * NULL).  Never NULL. */
 const char* vegas_last_error(const vegas_ctx* ctx);

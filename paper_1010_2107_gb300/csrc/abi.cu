@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <utility>
@@ -911,3 +912,237 @@ int vegas_ntheta(const vegas_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// One evaluation pass without any device allocation.
+//
+// Some callers cannot call cudaMalloc at all: code that runs inside another
+// runtime's memory pool with a fixed budget, or a latency-critical loop where
+// an allocation (which may synchronise the device or fail under
+// fragmentation) is not allowed after start-up.  vegas_eval_noalloc serves
+// them: the caller passes the grid and the output in its own device memory,
+// and every intermediate the pass needs (grid tables, integrand constants,
+// pass state, per-CTA partial sums) lives in the file-scope array below.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 8u << 20;  // 8 MiB, held by every GPU
+                                                    // that loads this library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+struct DerivedBlock {
+  double v[gv::kNumDerived];
+};
+
+__global__ void k_noalloc_params(DerivedBlock b, double* dst) {
+  for (int i = threadIdx.x; i < gv::kNumDerived; i += blockDim.x) dst[i] = b.v[i];
+}
+
+__global__ void k_noalloc_result(const GState* st, double* out) {
+  out[0] = st->last_I;
+  out[1] = st->last_var;
+  out[2] = st->last_sw;
+  out[3] = st->last_sw2;
+  out[4] = (double)st->last_nonfinite;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_integrand* fn,
+                                           const double* edges, uint32_t it, double* out) {
+  if (!cfg || !fn || !edges || !out) return thread_fail(VEGAS_EINVAL, "NULL argument");
+  const int d = cfg->ndim, N = cfg->nbins;
+  if (d < 1 || d > GVEGAS_MAXDIM) return thread_fail(VEGAS_EINVAL, "ndim %d outside 1..%d", d, GVEGAS_MAXDIM);
+  if (N < 2 || N > GVEGAS_MAXBINS) return thread_fail(VEGAS_EINVAL, "nbins %d outside 2..%d", N, GVEGAS_MAXBINS);
+  if (cfg->ncall < 2 || cfg->ncall > (int64_t)1 << 32)
+    return thread_fail(VEGAS_EINVAL, "ncall %lld outside 2..2^32", (long long)cfg->ncall);
+  if (cfg->precision < VG_FP64 || cfg->precision > VG_FP32_ACCCOMP)
+    return thread_fail(VEGAS_EINVAL, "unknown precision %d", cfg->precision);
+  if (it > 0x7FFFFFFFu) return thread_fail(VEGAS_EINVAL, "iteration index must be < 2^31");
+  const int ybits = cfg->ybits ? cfg->ybits : (cfg->precision == VG_FP64 ? 53 : 24);
+  if (ybits != 24 && ybits != 53) return thread_fail(VEGAS_EINVAL, "ybits must be 24 or 53");
+  if (fn->ndim != d) return thread_fail(VEGAS_EINVAL, "integrand ndim %d != config ndim %d", fn->ndim, d);
+  const int np = expected_nparams(fn->kind, d);
+  if (np < 0) return thread_fail(VEGAS_EINVAL, "unknown integrand kind %d", fn->kind);
+  if (fn->nparams != np || (np > 0 && !fn->params))
+    return thread_fail(VEGAS_EINVAL, "integrand kind %d needs %d parameters, got %d", fn->kind, np, fn->nparams);
+  const int g = cfg->nstrat < 1 ? 1 : cfg->nstrat;
+  uint64_t G = 1;
+  for (int a = 0; a < d; ++a) {
+    G *= (uint64_t)g;
+    if (G > (uint64_t)cfg->ncall) return thread_fail(VEGAS_EINVAL, "nstrat^ndim exceeds ncall");
+  }
+  if ((uint64_t)cfg->ncall % G != 0) return thread_fail(VEGAS_EINVAL, "ncall must be a multiple of nstrat^ndim");
+  if (G > 1 && (uint64_t)cfg->ncall / G < 2) return thread_fail(VEGAS_EINVAL, "need >= 2 points per hypercube");
+  if ((int64_t)g * N >= (ybits == 53 ? 2048 : (1 << 30)))
+    return thread_fail(VEGAS_EINVAL, "nstrat * nbins too large for %d-bit sampling", ybits);
+
+  DerivedBlock db;
+  double scale = 1.0;
+  char why_buf[128] = {0};
+  {
+    std::string why;
+    if (!derive_params(fn->kind, d, fn->params, db.v, &scale, &why)) {
+      snprintf(why_buf, sizeof why_buf, "%s", why.c_str());
+      return thread_fail(VEGAS_EINVAL, "%s", why_buf);
+    }
+  }
+  gv::KernelEntry ke{};
+  if (!lookup_kernel(fn->kind, cfg->precision, ybits, d, &ke))
+    return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
+  if (ke.sample_spec && d == ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256)
+    ke.sample = ke.sample_spec;
+
+  // Per-device set-up on the first call for the current device: the device
+  // address of the scratch array (its host-side name is only a stand-in).
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return thread_fail(VEGAS_EINVAL, "device index %d too large", dev);
+  unsigned char* scratch;
+  int sms;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      int n = 0;
+      e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "device attribute: %s", cudaGetErrorString(e));
+      g_noalloc_sms[dev] = n;
+      g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+    sms = g_noalloc_sms[dev];
+  }
+
+  // Launch shape (as for a context) with the CTA count bounded by the rows
+  // of partial sums that fit in the scratch array.
+  const int threads = 256;
+  int cap = 4;
+  while (cap < 64 && cap < (5 * threads) / (2 * N) + 4) cap *= 2;
+  int occ = 0;
+  size_t smem = 0;
+  for (;;) {
+    smem = ke.smem(d, N, cap);
+    occ = 0;
+    if (smem <= 227 * 1024) {
+      e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke.sample, threads, smem);
+      if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+    }
+    if (occ >= 1 || cap == 1) break;
+    cap /= 2;
+  }
+  if (occ < 1) return thread_fail(VEGAS_EINVAL, "sampling kernel does not fit in shared memory");
+  const int dN = d * N;
+  const size_t off_st = 0;
+  const size_t off_dp = align256(off_st + sizeof(GState));
+  const size_t off_t64 = align256(off_dp + sizeof(double) * gv::kNumDerived);
+  const size_t off_t32 = align256(off_t64 + sizeof(double2) * dN);
+  const size_t off_tot = align256(off_t32 + sizeof(float2) * dN);
+  const size_t off_rows = align256(off_tot + sizeof(double) * gv::kTotCols);
+  const size_t row_bytes = sizeof(double) * (2 * (size_t)dN + gv::kTotCols);
+  const int64_t max_rows = off_rows < kNoAllocScratchBytes ? (int64_t)((kNoAllocScratchBytes - off_rows - 512) / row_bytes) : 0;
+  if (max_rows < 1)
+    return thread_fail(VEGAS_EINVAL, "ndim * nbins = %d too large for the %zu-byte no-allocation scratch", dN,
+                       kNoAllocScratchBytes);
+  const uint64_t nc = (uint64_t)cfg->ncall / G;
+  const int strat = G > 1;
+  const int64_t cap_ctas = (int64_t)sms * occ;
+  int L = 1;
+  uint64_t units = (uint64_t)cfg->ncall;
+  if (strat) {
+    while (L < 32 && (uint64_t)(2 * L) <= nc && G * (uint64_t)L < 4 * (uint64_t)(cap_ctas * threads)) L *= 2;
+    units = G * (uint64_t)L;
+  }
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)((units + threads - 1) / threads), cap_ctas, max_rows}));
+  double* part_tot = reinterpret_cast<double*>(scratch + off_rows);
+  double* part_bins = reinterpret_cast<double*>(scratch + align256(off_rows + sizeof(double) * gv::kTotCols * ctas));
+  GState* st = reinterpret_cast<GState*>(scratch + off_st);
+
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  // Contents left by the previous call: the pass state must start cleared
+  // (its stop flag gates the kernels); tables, partial rows and totals are
+  // overwritten in full below.
+  e = cudaMemsetAsync(st, 0, offsetof(GState, hist), s);
+  if (e == cudaSuccess) {
+    k_noalloc_params<<<1, 128, 0, s>>>(db, reinterpret_cast<double*>(scratch + off_dp));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = gv_launch_tables(edges, d, N, reinterpret_cast<double2*>(scratch + off_t64),
+                         reinterpret_cast<float2*>(scratch + off_t32), s);
+  if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "no-allocation set-up: %s", cudaGetErrorString(e));
+
+  gv::SampleArgs A{};
+  A.d = d;
+  A.N = N;
+  A.g = g;
+  A.ybits = ybits;
+  A.lanes = L;
+  A.cap = cap;
+  A.strat = strat;
+  A.key0 = (uint32_t)cfg->seed;
+  A.key1 = (uint32_t)(cfg->seed >> 32);
+  A.instance = cfg->instance;
+  A.it_override = (int)it;
+  A.ncall = (uint64_t)cfg->ncall;
+  A.nc = (uint32_t)nc;
+  A.ncubes = (uint32_t)G;
+  A.cube_mul = (strat && (G & (G - 1)) == 0 && G > 1) ? 0x9E3779B1u : 1u;
+  A.g_pow2 = (g & (g - 1)) == 0;
+  A.g_log2 = 0;
+  while ((1 << A.g_log2) < g) ++A.g_log2;
+  A.t32 = (int64_t)g * N <= 256;
+  const double gb = (double)g * std::ldexp(1.0, ybits);
+  A.inv_gb_d = 1.0 / gb;
+  A.inv_gb_f = (float)(1.0 / gb);
+  A.inv_nc = 1.0 / (double)nc;
+  A.inv_nc1 = nc > 1 ? 1.0 / (double)(nc - 1) : 0.0;
+  A.nparts = ctas;
+  A.tab = cfg->precision == VG_FP64 ? (const void*)(scratch + off_t64) : (const void*)(scratch + off_t32);
+  A.dparams = reinterpret_cast<const double*>(scratch + off_dp);
+  A.st = st;
+  A.part_bins = part_bins;
+  A.part_tot = part_tot;
+  A.cubes = nullptr;
+  void* args[] = {&A};
+  e = cudaLaunchKernel(ke.sample, dim3(ctas), dim3(threads), args, smem, s);
+  gv::FinArgs F{};
+  F.d = d;
+  F.N = N;
+  F.nparts = ctas;
+  F.strat = strat;
+  F.refine = 0;
+  F.record = 0;
+  F.pair32 = cfg->precision == VG_FP32_ACCCOMP;
+  F.ncall = (uint64_t)cfg->ncall;
+  F.ncubes = G;
+  F.scale = scale;
+  F.alpha = cfg->alpha;
+  F.part_bins = part_bins;
+  F.part_tot = part_tot;
+  F.bins = out;
+  F.tot = reinterpret_cast<double*>(scratch + off_tot);
+  F.edges = nullptr;
+  F.tab64 = reinterpret_cast<double2*>(scratch + off_t64);
+  F.tab32 = reinterpret_cast<float2*>(scratch + off_t32);
+  F.st = st;
+  if (e == cudaSuccess) e = gv_launch_reduce(&F, s);
+  if (e == cudaSuccess) e = gv_launch_finalize(&F, s);
+  if (e == cudaSuccess) {
+    k_noalloc_result<<<1, 1, 0, s>>>(st, out + 2 * (size_t)dN);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "no-allocation pass: %s", cudaGetErrorString(e));
+  return VEGAS_OK;
+}

@@ -86,6 +86,8 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_microbench": (ctypes.c_int, [ctypes.c_int, _DP]),
+    "vegas_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
+                                          ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "vegas_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -286,6 +288,22 @@ def vegas_profile_pass(ctx: Context, n_pass: int = 10):
     ms = np.zeros(3)
     _check(lib().vegas_profile_pass(ctx.handle, int(n_pass), _dp(ms)), ctx.handle)
     return dict(sample=ms[0], reduce=ms[1], finalize=ms[2])
+
+
+def vegas_eval_noalloc(kind: int, ndim: int, params, edges_ptr: int, it: int, out_ptr: int, *,
+                       nbins: int = 50, ncall: int = 100_000, nstrat: int = 0, seed: int = 1,
+                       instance: int = 0, precision=FP64, ybits: int = 0, alpha: float = 1.5,
+                       stream=None):
+    """One evaluation pass on caller-owned device buffers (edges_ptr, out_ptr are
+    device addresses) without any device allocation; see include/gvegas.h."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    cfg = Config(int(ndim), int(nbins), int(ncall), 1, 0.0, float(alpha), int(nstrat), int(seed),
+                 int(instance), int(precision), int(ybits), _stream_handle(stream))
+    fn = IntegrandDesc(int(kind), int(ndim), _dp(p), len(p))
+    _check(lib().vegas_eval_noalloc(ctypes.byref(cfg), ctypes.byref(fn), ctypes.c_void_p(int(edges_ptr)),
+                                    int(it), ctypes.c_void_p(int(out_ptr))))
 
 
 MICROBENCH_OPS = {0: "ffma", 1: "imad_wide", 2: "dfma", 3: "mufu_ex2", 4: "i2f", 5: "philox_block",
