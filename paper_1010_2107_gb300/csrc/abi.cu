@@ -62,6 +62,9 @@ struct vegas_ctx {
   double* d_bins = nullptr;
   double* d_tot = nullptr;
   double* d_cubes = nullptr;
+  double* d_gpart = nullptr;  // adjoint partials [grad_nt + 2][grad_ctas] then totals
+  int grad_ctas = 0;
+  size_t grad_smem = 0;
   GState* d_st = nullptr;
   // host staging (pinned)
   GState* h_st = nullptr;
@@ -127,6 +130,7 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale,
       for (int i = 0; i < d; ++i) {
         dv[i] = p[i] * p[i];
         dv[M + i] = p[d + i];
+        dv[2 * M + i] = p[i];
       }
       return true;
     case VG_GENZ_PRODUCT_PEAK:
@@ -153,6 +157,7 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale,
       dv[S + 1] = p[1];
       dv[S + 2] = 1.0 / (w * w);
       dv[S + 3] = 0.5 * std::pow(w * std::sqrt(M_PI), -(double)d);
+      dv[S + 4] = w;
       return true;
     }
     case VG_RAMBO_BW: {
@@ -188,6 +193,10 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale,
       dv[gv::RB_T] = p[VG_RB_T] / rs;
       dv[gv::RB_INVWC] = cut == 1 ? rs / p[VG_RB_WC] : 0.0;
       dv[gv::RB_OBS] = obs;
+      dv[gv::RB_DMU_DM] = 2.0 * Mw / s;
+      dv[gv::RB_DMUG_DM] = Gw / s;
+      dv[gv::RB_DMUG_DG] = Mw / s;
+      dv[gv::RB_INVWC_GEV] = cut == 1 ? 1.0 / p[VG_RB_WC] : 0.0;
       // obs 0: V_n * s^-(n+1) (dimensionless product); 1: V_n; 2: V_n s;
       // 3: V_n / s.
       switch (obs) {
@@ -489,6 +498,7 @@ void vegas_destroy(vegas_ctx* c) {
   cudaFree(c->d_bins);
   cudaFree(c->d_tot);
   cudaFree(c->d_cubes);
+  cudaFree(c->d_gpart);
   cudaFree(c->d_st);
   if (c->h_st) cudaFreeHost(c->h_st);
   if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -589,6 +599,17 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
       cudaMemsetAsync(c->d_bins, 0, sizeof(double) * 2 * d * N, c->stream) != cudaSuccess)
     return bail(c->fail(VEGAS_ECUDA, "state initialisation failed"));
   if ((st = configure_launch(c))) return bail(st);
+  if (c->ke.grad) {  // adjoint pass (vegas_grad): launch shape and partial rows
+    c->grad_smem = c->ke.grad_smem(d, N);
+    int occg = 0;
+    e = cudaFuncSetAttribute(c->ke.grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->grad_smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occg, c->ke.grad, 256, c->grad_smem);
+    if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "adjoint launch: %s", cudaGetErrorString(e)));
+    const int64_t want = (cfg->ncall + 255) / 256;
+    c->grad_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->sm_count * std::max(occg, 1)));
+    if ((st = alloc((void**)&c->d_gpart, sizeof(double) * (size_t)(c->ke.grad_nt + 2) * (c->grad_ctas + 1))))
+      return bail(st);
+  }
   std::vector<double> e0((size_t)d * (N + 1));
   for (int a = 0; a < d; ++a)
     for (int k = 0; k <= N; ++k) e0[(size_t)a * (N + 1) + k] = (double)k / (double)N;
@@ -857,11 +878,34 @@ vegas_status vegas_get_launch(vegas_ctx* c, int* threads, int* ctas, int* ctas_p
 }
 
 vegas_status vegas_grad(vegas_ctx* c, uint32_t it, double* grad, double* I) {
-  (void)it;
-  (void)grad;
-  (void)I;
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  return c->fail(VEGAS_EINVAL, "gradient not available for this integrand");
+  if (!grad) return c->fail(VEGAS_EINVAL, "grad is NULL");
+  if (it > 0x7FFFFFFFu) return c->fail(VEGAS_EINVAL, "iteration index must be < 2^31");
+  const int nt = vegas_ntheta(c);
+  if (!c->ke.grad || nt == 0 || nt > c->ke.grad_nt)
+    return c->fail(VEGAS_EINVAL, "no adjoint kernel for integrand kind %d with ndim %d", c->kind, c->cfg.ndim);
+  if (c->kind == VG_RAMBO_BW && c->params[VG_RB_OBS] != 0.0)
+    return c->fail(VEGAS_EINVAL, "the RAMBO gradient is defined for the full integrand (observable 0)");
+  const int ncol = c->ke.grad_nt + 2;
+  gv::SampleArgs A = sample_args(c, (int)it);
+  double* part = c->d_gpart;
+  double* out = c->d_gpart + (size_t)ncol * c->grad_ctas;
+  void* args[] = {&A, &part};
+  CK(c, cudaLaunchKernel(c->ke.grad, dim3(c->grad_ctas), dim3(256), args, c->grad_smem, c->stream));
+  CK(c, gv_launch_colsum(part, ncol, c->grad_ctas, out, c->stream));
+  vegas_status st = stage(c, ncol);
+  if (st) return st;
+  CK(c, cudaMemcpyAsync(c->h_stage, out, ncol * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const double k = c->scale / (double)c->cfg.ncall;
+  const int d = c->cfg.ndim, DM = c->ke.dm;
+  for (int t = 0; t < nt; ++t) {
+    // the Genz Gaussian kernel stores du at [0, d) and da at [DM, DM + d)
+    const int src = (c->kind == VG_GENZ_GAUSSIAN && t >= d) ? DM + (t - d) : t;
+    grad[t] = c->h_stage[src] * k;
+  }
+  if (I) *I = c->h_stage[c->ke.grad_nt] * k;
+  return VEGAS_OK;
 }
 
 vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {

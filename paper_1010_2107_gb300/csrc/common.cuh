@@ -13,7 +13,7 @@ namespace gv {
 constexpr int kMaxDim = GVEGAS_MAXDIM;
 constexpr int kMaxBins = GVEGAS_MAXBINS;
 constexpr int kMaxHist = GVEGAS_MAXHIST;
-constexpr int kNumDerived = 2 * kMaxDim + 16;  // derived integrand constants
+constexpr int kNumDerived = 3 * kMaxDim + 24;  // derived integrand constants
 constexpr int kTotCols = 8;                     // per-CTA totals columns
 
 // Columns of the per-CTA totals block.

@@ -212,6 +212,19 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs F) {
   }
 }
 
+// Column sums of a [ncols][nrows] partial block (one warp per column,
+// lanes stride the rows, fixed xor butterfly).
+__global__ void __launch_bounds__(256) k_colsum(const double* part, int ncols, int nrows, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  double acc = 0.0;
+  for (int r = lane; r < nrows; r += 32) acc += part[(size_t)col * nrows + r];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) out[col] = acc;
+}
+
 // Window / stop-flag bookkeeping between passes (one thread).
 __global__ void k_control(GState* st, int ops, double acc) {
   if (ops & CTL_SNAPSHOT) {
@@ -266,6 +279,11 @@ cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s) {
 
 cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s) {
   gv::k_finalize<<<F->d + 1, 64, 0, s>>>(*F);
+  return cudaGetLastError();
+}
+
+cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s) {
+  gv::k_colsum<<<(ncols + 7) / 8, 256, 0, s>>>(part, ncols, nrows, out);
   return cudaGetLastError();
 }
 

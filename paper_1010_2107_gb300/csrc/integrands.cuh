@@ -15,9 +15,15 @@ namespace gv {
 __device__ __forceinline__ float gexp(float x) { return __expf(x); }
 __device__ __forceinline__ double gexp(double x) { return exp(x); }
 
-// Derived-constant slots.  Genz / Gaussian: a-like values at [0, DM),
-// u-like values at [kMaxDim, kMaxDim + d), scalars from kScalar on.
-constexpr int kScalar = 2 * kMaxDim;
+// Derived-constant slots.  Genz / Gaussian: a-like values at [0, d),
+// u-like values at [kMaxDim, kMaxDim + d), raw a_i at [2 kMaxDim, ...),
+// scalars from kScalar on.
+constexpr int kScalar = 3 * kMaxDim;
+
+// Integrands with an analytic parameter gradient define
+//   static T grad(x, d, P, g)  ->  f(x), with g[t] = df/dtheta_t
+// in the units of the integrand's own (dimensionless) value; NT is the
+// largest number of parameters for a compile-time bound DM.
 
 // ----------------------------------------------------------------- Genz
 // f = exp(-sum a_i^2 (x_i - u_i)^2).  P[i] = a_i^2, P[kMaxDim+i] = u_i.
@@ -32,6 +38,20 @@ struct GenzGaussian {
         q = vfma(P[a] * t, t, q);
       }
     return gexp(-q);
+  }
+  // theta = (u_1..u_d, a_1..a_d): df/du_i = 2 a_i^2 (x_i - u_i) f,
+  // df/da_i = -2 a_i (x_i - u_i)^2 f.
+  static constexpr int NT = 2 * DM;
+  static __device__ __forceinline__ T grad(const T (&x)[DM], int d, const T* P, T* g) {
+    const T f = eval(x, d, P);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t = x[a] - P[kMaxDim + a];
+        g[a] = T(2) * P[a] * t * f;
+        g[DM + a] = T(-2) * P[2 * kMaxDim + a] * t * t * f;
+      }
+    return f;
   }
 };
 
@@ -92,6 +112,29 @@ struct DoubleGaussian {
     const T iw2 = P[kScalar + 2];
     return P[kScalar + 3] * (gexp(-q1 * iw2) + gexp(-q2 * iw2));
   }
+  // theta = (c1, c2, w): df/dc_k = K/2 E_k 2 sum_i (x_i - c_k) / w^2,
+  // df/dw = K/2 sum_k E_k (2 q_k / w^3 - d / w), q_k = sum_i (x_i - c_k)^2.
+  static constexpr int NT = 3;
+  static __device__ __forceinline__ T grad(const T (&x)[DM], int d, const T* P, T* g) {
+    const T c1 = P[kScalar], c2 = P[kScalar + 1], iw2 = P[kScalar + 2], K2 = P[kScalar + 3];
+    const T w = P[kScalar + 4];
+    T q1 = T(0), q2 = T(0), l1 = T(0), l2 = T(0);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t1 = x[a] - c1, t2 = x[a] - c2;
+        q1 = vfma(t1, t1, q1);
+        q2 = vfma(t2, t2, q2);
+        l1 += t1;
+        l2 += t2;
+      }
+    const T e1 = K2 * gexp(-q1 * iw2), e2 = K2 * gexp(-q2 * iw2);
+    g[0] = e1 * T(2) * l1 * iw2;
+    g[1] = e2 * T(2) * l2 * iw2;
+    const T iw = T(1) / w;
+    g[2] = e1 * (T(2) * q1 * iw2 * iw - T(d) * iw) + e2 * (T(2) * q2 * iw2 * iw - T(d) * iw);
+    return e1 + e2;
+  }
 };
 
 // ----------------------------------------------------------------- RAMBO
@@ -104,7 +147,11 @@ struct DoubleGaussian {
 // which has no cancellation for nearly collinear pairs in FP32.
 enum {
   RB_N = kScalar, RB_MU, RB_MUG, RB_MUG2, RB_PTMIN, RB_DR2, RB_CUT, RB_T,
-  RB_INVWC, RB_OBS
+  RB_INVWC, RB_OBS,
+  RB_DMU_DM,    // d mu / dM = 2 M / s            (per GeV)
+  RB_DMUG_DM,   // d mu_g / dM = Gamma / s        (per GeV)
+  RB_DMUG_DG,   // d mu_g / dGamma = M / s        (per GeV)
+  RB_INVWC_GEV  // 1 / w_c                        (per GeV)
 };
 
 template <typename T, int DM>
@@ -218,6 +265,63 @@ struct RamboBW {
     for (int i = 1; i < NM; ++i)
       if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
     return cw * b / den;
+  }
+
+  // theta = (M, Gamma, T) in GeV for the full integrand (obs 0).  The Breit-
+  // Wigner factor b = mu_g / ((s12 - mu)^2 + mu_g^2) depends on M through mu
+  // and mu_g and on Gamma through mu_g; the sigmoid cut gives
+  // d ln(cut)/dT = -sum_i (1 - sigma_i) / w_c; the hard cut has dT = 0.
+  static constexpr int NT = 3;
+  static __device__ __forceinline__ T grad(const T (&x)[DM], int d, const T* P, T* g) {
+    g[0] = g[1] = g[2] = T(0);
+    const int obs = (int)P[RB_OBS];
+    if (obs != 0) return eval(x, d, P);
+    const int n = d >> 2;
+    Event ev;
+    if (!kinematics(x, n, ev)) return T(0);
+    const int cut = (int)P[RB_CUT];
+    T cw = T(1), dlc = T(0);
+    if (cut == 0) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n && !(ev.pt[i] > P[RB_PTMIN])) return T(0);
+    } else if (cut == 1) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) {
+          const T sg = T(1) / (T(1) + vexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
+          cw *= sg;
+          dlc -= (T(1) - sg) * P[RB_INVWC_GEV];
+        }
+    }
+    if (cut != 2) {
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NM; ++j)
+          if (j < n) {
+            const T de = ev.eta[i] - ev.eta[j];
+            const T dp = wrap_dphi(ev.phi[i] - ev.phi[j]);
+            if (!(vfma(de, de, dp * dp) > P[RB_DR2])) return T(0);
+          }
+    }
+    const T s12 = sij(ev, 0, 1);
+    T den = s12;
+#pragma unroll
+    for (int i = 1; i < NM; ++i)
+      if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
+    const T t = s12 - P[RB_MU], mug = P[RB_MUG];
+    const T D = vfma(t, t, P[RB_MUG2]);
+    const T b = mug / D;
+    const T pre = cw / den;
+    // db/dM = (mug' D - mug D') / D^2, D' = -2 t mu' + 2 mug mug'
+    const T dDdM = T(-2) * t * P[RB_DMU_DM] + T(2) * mug * P[RB_DMUG_DM];
+    const T dDdG = T(2) * mug * P[RB_DMUG_DG];
+    g[0] = pre * (P[RB_DMUG_DM] * D - mug * dDdM) / (D * D);
+    g[1] = pre * (P[RB_DMUG_DG] * D - mug * dDdG) / (D * D);
+    const T f = pre * b;
+    g[2] = f * dlc;
+    return f;
   }
 };
 

@@ -19,6 +19,9 @@ struct KernelEntry {
   size_t (*smem)(int d, int N, int cap);  // dynamic shared memory of `sample`
                                           // with bucket capacity cap
   int dm;                             // compile-time dimension bound
+  const void* grad;                   // k_grad<T, DM, F, YB> or null
+  int grad_nt;                        // its gradient columns (F<T, DM>::NT)
+  size_t (*grad_smem)(int d, int N);
 };
 
 // Per-kind registries (one per random-bit width); false when no
@@ -53,6 +56,7 @@ struct DumpArgs {
 extern "C" {
 cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s);
+cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);
 cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
 cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s);
 cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,

@@ -515,6 +515,121 @@ __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
   if (D.f) D.f[i] = (double)f;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint pass: the gradient of the iteration estimate with respect to the
+// integrand parameters on a frozen grid, with the random numbers of one
+// iteration (common random numbers):  dI/dtheta = (1/NCALL) sum_s J_s
+// df/dtheta(x_s).  Each CTA writes one partial row per column: the NT
+// gradient sums, then sum w and sum w^2 (FP64, or compensated FP32 pairs
+// converted once per CTA).
+// ---------------------------------------------------------------------------
+template <template <typename, int> class F> struct HasGrad { static constexpr bool value = false; };
+template <> struct HasGrad<GenzGaussian> { static constexpr bool value = true; };
+template <> struct HasGrad<DoubleGaussian> { static constexpr bool value = true; };
+template <> struct HasGrad<RamboBW> { static constexpr bool value = true; };
+
+template <typename T, int DM, template <typename, int> class F, int YB>
+__global__ void __launch_bounds__(256) k_grad(const SampleArgs A, double* part) {
+  using T2 = typename Vec2<T>::type;
+  constexpr int NT = F<T, DM>::NT;
+  constexpr int NC = NT + 2;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  const int d = A.d, N = A.N, dN = d * N;
+  const uint32_t it = (uint32_t)A.it_override;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T2* tab = reinterpret_cast<T2*>(smem);
+  T* P = reinterpret_cast<T*>(smem + (size_t)dN * sizeof(T2));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T2* gtab = reinterpret_cast<const T2*>(A.tab);
+  for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
+  for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
+  __syncthreads();
+
+  double accd[NC];
+  fpair accf[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    accd[q] = 0.0;
+    accf[q] = fpair{0.f, 0.f};
+  }
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + tid; s < A.ncall; s += stride) {
+    int cd[DM];
+    uint32_t rest = A.strat ? (uint32_t)(s / A.nc) : 0u;
+#pragma unroll
+    for (int a = 0; a < DM; ++a) {
+      cd[a] = 0;
+      if (a < d && A.strat) {
+        cd[a] = (int)(rest % (uint32_t)A.g);
+        rest /= (uint32_t)A.g;
+      }
+    }
+    T x[DM];
+    int kb[DM];
+    const T J = make_point<T, DM, YB>(A, it, (uint32_t)s, cd, tab, x, kb, nullptr);
+    T g[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) g[q] = T(0);
+    const T f = F<T, DM>::grad(x, d, P, g);
+    const T w = f * J;
+    if (!vfinite(w)) continue;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const T v = q < NT ? g[q] * J : (q == NT ? w : w * w);
+      if (!vfinite(v)) continue;
+      if (F32)
+        comp_add(accf[q], (float)v);
+      else
+        accd[q] += (double)v;
+    }
+  }
+  __shared__ double red[8][NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    double v;
+    if (F32) {
+      fpair p = accf[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        fpair o;
+        o.hi = __shfl_xor_sync(0xffffffffu, p.hi, off);
+        o.lo = __shfl_xor_sync(0xffffffffu, p.lo, off);
+        comp_merge(p, o);
+      }
+      v = comp_value(p);
+    } else {
+      v = accd[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    }
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  for (int q = tid; q < NC; q += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += red[w][q];
+    part[(size_t)q * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+template <typename T>
+inline size_t grad_smem_bytes(int d, int N) {
+  return (size_t)d * N * sizeof(typename Vec2<T>::type) + kNumDerived * sizeof(T);
+}
+
+template <typename T, int DM, template <typename, int> class F, int YB>
+inline void grad_entry(KernelEntry& e) {
+  if constexpr (HasGrad<F>::value && (DM <= 20)) {
+    e.grad = (const void*)&k_grad<T, DM, F, YB>;
+    e.grad_nt = F<T, DM>::NT;
+    e.grad_smem = &grad_smem_bytes<T>;
+  } else {
+    e.grad = nullptr;
+    e.grad_nt = 0;
+    e.grad_smem = nullptr;
+  }
+}
+
 template <typename T, int DM, template <typename, int> class F, int ACC, int YB>
 inline const void* spec_kernel() {
   if constexpr (YB == 24 && ACC != 1)
@@ -528,6 +643,7 @@ inline KernelEntry make_entry() {
   KernelEntry e;
   e.sample = (const void*)&k_sample<T, DM, F, ACC, YB, false>;
   e.sample_spec = spec_kernel<T, DM, F, ACC, YB>();
+  grad_entry<T, DM, F, YB>(e);
   e.dump = (const void*)&k_dump<T, DM, F, YB>;
   e.smem = &sample_smem_bytes<T, ACC>;
   e.dm = DM;
