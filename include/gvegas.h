@@ -245,6 +245,54 @@ vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
  * finalisation.  Synchronises the stream. */
 vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
 
+/* ------------------------------------------------------------------------
+ * Batched integration: n independent VEGAS integrations iterated together,
+ * each iteration one persistent kernel over all instances plus one
+ * finalisation kernel (the loop of Sec. 2.1, steps 2-6, for every
+ * instance), a whole call captured in one CUDA graph.
+ *
+ * Instances share precision (VG_FP64 or VG_FP32_ACCCOMP), ybits, nbins and
+ * seed; each has its own integrand (any kind but VG_RAMBO_BW), ndim
+ * (1..16), ncall (< 2^32), alpha and `instance` id (Philox counter word 3,
+ * so instance i draws the points a standalone context with the same id
+ * draws).  No stratification and no ACC stop.  The stream of cfgs[0] (or a
+ * stream the batch creates) orders all work.
+ * ------------------------------------------------------------------------ */
+typedef struct vegas_batch vegas_batch;
+
+vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_integrand* integrands,
+                                vegas_batch** out);
+void vegas_batch_destroy(vegas_batch* batch);
+
+/* n_iter iterations (0..64) of every instance, refining after each when
+ * refine != 0; out (nullable) receives one result per instance (combined
+ * over the instance's window) and forces a synchronisation. */
+vegas_status vegas_batch_iterate(vegas_batch* batch, int n_iter, int refine, vegas_result* out);
+
+/* Uniform grids, empty windows and iteration counters back to zero. */
+vegas_status vegas_batch_reset(vegas_batch* batch);
+
+/* Grid edges [ndim_i][nbins+1] and (nullable) per-bin sums of the last
+ * iteration [2][ndim_i][nbins] of instance i; its history (I_j, sigma_j^2). */
+vegas_status vegas_batch_get_grid(vegas_batch* batch, int i, double* edges, double* bin_sums);
+vegas_status vegas_batch_get_history(vegas_batch* batch, int i, double* hist, int max_iters, int* n_out);
+
+/* Launch shape: threads per CTA (64..256, multiple of 32) and rounds per
+ * work item (an item is threads * rounds points of one instance). */
+vegas_status vegas_batch_set_launch(vegas_batch* batch, int threads, int rounds);
+vegas_status vegas_batch_get_launch(vegas_batch* batch, int* threads, int* rounds, int* ctas, int* items);
+
+/* Autotuner: times every (threads, rounds) candidate on the batch's own
+ * workload (an evaluation pass, nothing recorded) and keeps the fastest;
+ * returns it and its sampling-kernel milliseconds. */
+vegas_status vegas_batch_autotune(vegas_batch* batch, int* threads, int* rounds, double* ms);
+
+/* Mean milliseconds of the sampling kernel (ms[0]) and the finalisation
+ * (ms[1]) over n_pass evaluation passes (nothing recorded, no refinement). */
+vegas_status vegas_batch_profile(vegas_batch* batch, int n_pass, double* ms);
+
+const char* vegas_batch_last_error(const vegas_batch* batch);
+
 /* Measured issue rate of one instruction class on the current device, in
  * thread-operations per second summed over all SMs (no counterpart in the
  * paper; these are the denominators of the ALU roofline).  op: 0 FP32 FMA,

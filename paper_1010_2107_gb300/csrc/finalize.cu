@@ -9,6 +9,7 @@
 //               inverse-variance combination, chi^2 and the ACC test.
 #include "common.cuh"
 #include "kernels.h"
+#include "refine.cuh"
 
 namespace gv {
 
@@ -62,77 +63,10 @@ __global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
   if (lane == 0) *dst = acc * sc;
 }
 
-// Neumaier compensated accumulation (same scheme as the CPU oracle).
-struct KSum {
-  double s = 0.0, c = 0.0;
-  __device__ void add(double v) {
-    const double t = s + v;
-    if (fabs(s) >= fabs(v))
-      c += (s - t) + v;
-    else
-      c += (v - t) + s;
-    s = t;
-  }
-  __device__ double value() const { return s + c; }
-};
-
 __device__ void refine_axis(const FinArgs& F, int a) {
-  __shared__ double dsm[kMaxBins], r[kMaxBins], e[kMaxBins + 1], enew[kMaxBins + 1];
-  __shared__ int skip;
-  const int N = F.N, tid = threadIdx.x;
-  const double* dd = F.bins + (size_t)F.d * N + (size_t)a * N;  // S2[a][*]
-  double* ea = F.edges + (size_t)a * (N + 1);
-  for (int k = tid; k <= N; k += blockDim.x) e[k] = ea[k];
-  for (int k = tid; k < N; k += blockDim.x) {
-    double v;
-    if (N == 2)
-      v = (dd[0] + dd[1]) / 2.0;
-    else if (k == 0)
-      v = (dd[0] + dd[1]) / 2.0;
-    else if (k == N - 1)
-      v = (dd[N - 2] + dd[N - 1]) / 2.0;
-    else
-      v = (dd[k - 1] + dd[k] + dd[k + 1]) / 3.0;
-    dsm[k] = v;
-  }
-  __syncthreads();
-  __shared__ double D;
-  if (tid == 0) {
-    double s = 0.0;
-    for (int k = 0; k < N; ++k) s += dsm[k];
-    D = s;
-    skip = !(s > 0.0) || !isfinite(s);
-  }
-  __syncthreads();
-  if (skip) return;
-  for (int k = tid; k < N; k += blockDim.x) {
-    const double x = dsm[k];
-    r[k] = x <= 0.0 ? 0.0 : (x >= D ? 1.0 : pow((1.0 - x / D) / log(D / x), F.alpha));
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double R = 0.0;
-    for (int k = 0; k < N; ++k) R += r[k];
-    enew[0] = 0.0;
-    enew[N] = 1.0;
-    int k = 0;
-    double acc = 0.0;
-    for (int j = 1; j < N; ++j) {
-      const double tau = (double)j * R / (double)N;
-      while (k < N - 1 && acc + r[k] < tau) {
-        acc += r[k];
-        ++k;
-      }
-      enew[j] = e[k] + (tau - acc) / r[k] * (e[k + 1] - e[k]);
-    }
-  }
-  __syncthreads();
-  for (int k = tid; k <= N; k += blockDim.x) ea[k] = enew[k];
-  for (int k = tid; k < N; k += blockDim.x) {
-    const double lo = enew[k], w = enew[k + 1] - enew[k];
-    F.tab64[(size_t)a * N + k] = make_double2(lo, w);
-    F.tab32[(size_t)a * N + k] = make_float2((float)lo, (float)w);
-  }
+  const int N = F.N;
+  refine_axis_core(F.bins + (size_t)F.d * N + (size_t)a * N, F.edges + (size_t)a * (N + 1),
+                   F.tab64 + (size_t)a * N, F.tab32 + (size_t)a * N, N, F.alpha);
 }
 
 __device__ void record_iteration(const FinArgs& F) {
@@ -165,33 +99,8 @@ __device__ void record_iteration(const FinArgs& F) {
   st->samples += (long long)F.ncall;
   st->it += 1;
   // Inverse-variance combination over the window (Lepage).
-  int nzero = 0;
-  KSum z;
-  for (int j = 0; j < h; ++j)
-    if (!(st->hist[j][1] > 0.0)) {
-      z.add(st->hist[j][0]);
-      ++nzero;
-    }
-  double Ib = 0.0, sg = 0.0, chi = 0.0;
-  if (nzero > 0) {
-    Ib = z.value() / (double)nzero;
-  } else if (h > 0) {
-    KSum sw, swi;
-    for (int j = 0; j < h; ++j) {
-      sw.add(1.0 / st->hist[j][1]);
-      swi.add(st->hist[j][0] / st->hist[j][1]);
-    }
-    Ib = swi.value() / sw.value();
-    sg = 1.0 / sqrt(sw.value());
-    if (h > 1) {
-      KSum c2;
-      for (int j = 0; j < h; ++j) {
-        const double dv = st->hist[j][0] - Ib;
-        c2.add(dv * dv / st->hist[j][1]);
-      }
-      chi = c2.value() / (double)(h - 1);
-    }
-  }
+  double Ib, sg, chi;
+  combine_history(st->hist, h, &Ib, &sg, &chi);
   st->I = Ib;
   st->sigma = sg;
   st->chi2 = chi;

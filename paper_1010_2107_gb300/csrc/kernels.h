@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace gv {
@@ -38,6 +40,12 @@ bool entries_dgauss_y24(int prec, int d, KernelEntry* out);
 bool entries_dgauss_y53(int prec, int d, KernelEntry* out);
 bool entries_rambo_y24(int prec, int d, KernelEntry* out);
 bool entries_rambo_y53(int prec, int d, KernelEntry* out);
+
+// Number of parameters the integrand `kind` takes in `d` dimensions (-1 for
+// an unknown kind), and the constants its device code reads (`dv`, length
+// kNumDerived) plus the output scale; false with a reason when invalid.
+int expected_nparams(int kind, int d);
+bool derive_params(int kind, int d, const double* p, double* dv, double* scale, std::string* why);
 
 // Arguments of the per-sample dump kernel.
 struct DumpArgs {

@@ -152,28 +152,125 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   return J;
 }
 
-// Shared memory layout of k_sample (byte offsets): grid table, integrand
-// constants, bucket counters [d N] (int), buckets [cap][d N] (H), the
-// overflow histogram [2][d][N] (H, atomics), the CTA histogram [2][d][N]
-// (H), and for ACC 2 its compensated pairs [2][d][N].
-template <typename T, int ACC>
-struct SmemLayout {
-  using H = typename AccTraits<ACC>::H;
-  static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
-  static __host__ __device__ size_t params(int dN) { return (size_t)dN * sizeof(typename Vec2<T>::type); }
-  static __host__ __device__ size_t cnt(int dN) { return a16(params(dN) + kNumDerived * sizeof(T)); }
-  static __host__ __device__ size_t bucket(int dN) { return a16(cnt(dN) + (size_t)dN * sizeof(int)); }
-  static __host__ __device__ size_t ovf(int dN, int cap) { return a16(bucket(dN) + (size_t)cap * dN * sizeof(H)); }
-  static __host__ __device__ size_t cta(int dN, int cap) { return a16(ovf(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
-  static __host__ __device__ size_t comp(int dN, int cap) { return a16(cta(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
-  static __host__ __device__ size_t total(int dN, int cap) {
-    return comp(dN, cap) + (ACC == 2 ? 2 * (size_t)dN * sizeof(fpair) : 0);
-  }
-};
-
 // Tiles between compensated folds of the CTA histogram (ACC 2): the plain
 // FP32 cells then add at most this many bucket sums.
 constexpr int kFoldTiles = 8;
+
+// Bucketed tile histogram of one CTA (shared memory).  Shared-memory float
+// atomics are compare-and-swap loops on this GPU while 32-bit integer
+// atomics are native, so a point claims a slot of each of its (axis, bin)
+// buckets with one integer atomicAdd and stores w there (scatter); at the end
+// of a tile one thread per cell sums its bucket into the CTA's cells, w and
+// w^2 (gather).  Full buckets spill into an overflow histogram.  Layout from
+// the base: counters [d N] (int), buckets [cap][d N] (H), overflow [2][d N]
+// (H), cells [2][d N] (H), and for ACC 2 compensated pairs [2][d N].
+template <int ACC>
+struct TileHist {
+  using H = typename AccTraits<ACC>::H;
+  static constexpr bool COMP = ACC == 2;
+  static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
+  static __host__ __device__ size_t off_bucket(int dN) { return a16((size_t)dN * sizeof(int)); }
+  static __host__ __device__ size_t off_ovf(int dN, int cap) { return a16(off_bucket(dN) + (size_t)cap * dN * sizeof(H)); }
+  static __host__ __device__ size_t off_cta(int dN, int cap) { return a16(off_ovf(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
+  static __host__ __device__ size_t off_comp(int dN, int cap) { return a16(off_cta(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
+  static __host__ __device__ size_t bytes(int dN, int cap) {
+    return off_comp(dN, cap) + (COMP ? 2 * (size_t)dN * sizeof(fpair) : 0);
+  }
+
+  int* cnt;
+  H* bucket;  // [cap][d N]: slot-major, so a gather over consecutive cells is conflict-free
+  H* ovf;
+  H* cta;
+  fpair* cmp;
+  int N, dN, cap, tile;
+
+  __device__ __forceinline__ void bind(unsigned char* base, int dN_, int N_, int cap_) {
+    dN = dN_;
+    N = N_;
+    cap = cap_;
+    tile = 0;
+    cnt = reinterpret_cast<int*>(base);
+    bucket = reinterpret_cast<H*>(base + off_bucket(dN));
+    ovf = reinterpret_cast<H*>(base + off_ovf(dN, cap));
+    cta = reinterpret_cast<H*>(base + off_cta(dN, cap));
+    cmp = reinterpret_cast<fpair*>(base + off_comp(dN, cap));
+  }
+  // Clear everything (the caller synchronises before the first scatter).
+  __device__ __forceinline__ void zero(int tid, int nthr) {
+    for (int i = tid; i < dN; i += nthr) cnt[i] = 0;
+    for (int i = tid; i < 2 * dN; i += nthr) {
+      ovf[i] = H(0);
+      cta[i] = H(0);
+      if (COMP) cmp[i] = fpair{0.f, 0.f};
+    }
+  }
+  template <int DM>
+  __device__ __forceinline__ void scatter(const int (&kb)[DM], int d, H w) {
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const int cell = a * N + kb[a];
+        const int pos = atomicAdd(&cnt[cell], 1);
+        if (pos < cap) {
+          bucket[pos * dN + cell] = w;
+        } else {
+          atomicAdd(&ovf[cell], w);
+          atomicAdd(&ovf[dN + cell], w * w);
+        }
+      }
+  }
+  // End of a tile (all threads of the CTA); ACC 2 folds the FP32 cells into
+  // the compensated pairs every kFoldTiles tiles.
+  __device__ __forceinline__ void gather(int tid, int nthr) {
+    __syncthreads();
+    const bool fold = COMP && (++tile % kFoldTiles == 0);
+    for (int cell = tid; cell < dN; cell += nthr) {
+      const int n = min(cnt[cell], cap);
+      H s1 = H(0), s2 = H(0);
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        const H v0 = bucket[j * dN + cell], v1 = bucket[(j + 1) * dN + cell];
+        const H v2 = bucket[(j + 2) * dN + cell], v3 = bucket[(j + 3) * dN + cell];
+        s1 += (v0 + v1) + (v2 + v3);
+        s2 += (v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3);
+      }
+      for (; j < n; ++j) {
+        const H v = bucket[j * dN + cell];
+        s1 += v;
+        s2 += v * v;
+      }
+      H c1 = cta[cell] + s1, c2 = cta[dN + cell] + s2;
+      if (fold) {
+        comp_add(cmp[cell], (float)c1);
+        comp_add(cmp[dN + cell], (float)c2);
+        c1 = c2 = H(0);
+      }
+      cta[cell] = c1;
+      cta[dN + cell] = c2;
+      cnt[cell] = 0;
+    }
+    __syncthreads();
+  }
+  // Final value of cell i in [0, 2 d N) (after a gather): a compensated pair
+  // (ACC 2) or a double.
+  __device__ __forceinline__ fpair pair(int i) const {
+    fpair p = cmp[i];
+    comp_add(p, (float)cta[i]);
+    comp_add(p, (float)ovf[i]);
+    return p;
+  }
+  __device__ __forceinline__ double value(int i) const { return (double)cta[i] + (double)ovf[i]; }
+};
+
+// Shared memory layout of k_sample (byte offsets): grid table, integrand
+// constants, then the tile histogram.
+template <typename T, int ACC>
+struct SmemLayout {
+  static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
+  static __host__ __device__ size_t params(int dN) { return (size_t)dN * sizeof(typename Vec2<T>::type); }
+  static __host__ __device__ size_t hist(int dN) { return a16(params(dN) + kNumDerived * sizeof(T)); }
+  static __host__ __device__ size_t total(int dN, int cap) { return hist(dN) + TileHist<ACC>::bytes(dN, cap); }
+};
 
 // Warp all-reduce of a compensated pair (fixed xor order).
 __device__ __forceinline__ fpair warp_sum(fpair p) {
@@ -203,22 +300,14 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + L::params(dN));
-  int* cnt = reinterpret_cast<int*>(smem + L::cnt(dN));
-  H* bucket = reinterpret_cast<H*>(smem + L::bucket(dN));   // [cap][d N]
-  H* ovf = reinterpret_cast<H*>(smem + L::ovf(dN, cap));     // [2][d N]
-  H* cta = reinterpret_cast<H*>(smem + L::cta(dN, cap));     // [2][d N]
-  fpair* cmp = reinterpret_cast<fpair*>(smem + L::comp(dN, cap));  // ACC 2: [2][d N]
+  TileHist<ACC> hist;
+  hist.bind(smem + L::hist(dN), dN, N, cap);
 
   // Coalesced, vectorised grid-table load (one 8- or 16-byte cell per bin).
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
-  for (int i = tid; i < dN; i += blockDim.x) cnt[i] = 0;
-  for (int i = tid; i < 2 * dN; i += blockDim.x) {
-    ovf[i] = H(0);
-    cta[i] = H(0);
-    if (COMP) cmp[i] = fpair{0.f, 0.f};
-  }
+  hist.zero(tid, blockDim.x);
   __syncthreads();
 
   int nonfinite = 0;
@@ -226,58 +315,8 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
 #pragma unroll
   for (int a = 0; a < DM; ++a) cd[a] = 0;
 
-  // Bucketed tile histogram (shared-memory float atomics are compare-and-
-  // swap loops on this GPU, 32-bit integer atomics are native): a point
-  // claims a slot of its (axis, bin) bucket with one integer atomicAdd and
-  // stores w there; full buckets spill into the overflow histogram.
-  auto scatter = [&](const int (&kb)[DM], H w) {
-#pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) {
-        const int cell = a * N + kb[a];
-        const int pos = atomicAdd(&cnt[cell], 1);
-        if (pos < cap) {
-          bucket[pos * dN + cell] = w;
-        } else {
-          atomicAdd(&ovf[cell], w);
-          atomicAdd(&ovf[dN + cell], w * w);
-        }
-      }
-  };
-  // End of a tile: one thread per cell sums its bucket (w and w^2) into the
-  // CTA histogram; the bucket layout [slot][cell] keeps this conflict-free.
-  // ACC 2 folds the FP32 cells into compensated pairs every kFoldTiles.
-  int tile = 0;
-  auto gather = [&]() {
-    __syncthreads();
-    const bool fold = COMP && (++tile % kFoldTiles == 0);
-    for (int cell = tid; cell < dN; cell += blockDim.x) {
-      const int n = min(cnt[cell], cap);
-      H s1 = H(0), s2 = H(0);
-      int j = 0;
-      for (; j + 4 <= n; j += 4) {
-        const H v0 = bucket[j * dN + cell], v1 = bucket[(j + 1) * dN + cell];
-        const H v2 = bucket[(j + 2) * dN + cell], v3 = bucket[(j + 3) * dN + cell];
-        s1 += (v0 + v1) + (v2 + v3);
-        s2 += (v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3);
-      }
-      for (; j < n; ++j) {
-        const H v = bucket[j * dN + cell];
-        s1 += v;
-        s2 += v * v;
-      }
-      H c1 = cta[cell] + s1, c2 = cta[dN + cell] + s2;
-      if (fold) {
-        comp_add(cmp[cell], (float)c1);
-        comp_add(cmp[dN + cell], (float)c2);
-        c1 = c2 = H(0);
-      }
-      cta[cell] = c1;
-      cta[dN + cell] = c2;
-      cnt[cell] = 0;
-    }
-    __syncthreads();
-  };
+  auto scatter = [&](const int (&kb)[DM], H w) { hist.template scatter<DM>(kb, d, w); };
+  auto gather = [&]() { hist.gather(tid, blockDim.x); };
   // w = f J in the kernel precision, widened to the histogram type H
   // (squares are then formed in H: FP64 unless ACC == 2).
   auto eval_point = [&](uint32_t s, int (&kb)[DM]) -> H {
@@ -425,12 +464,10 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   const int np = A.nparts, row = blockIdx.x;
   for (int i = tid; i < 2 * dN; i += blockDim.x) {
     if constexpr (COMP) {
-      fpair p = cmp[i];
-      comp_add(p, (float)cta[i]);
-      comp_add(p, (float)ovf[i]);
+      const fpair p = hist.pair(i);
       reinterpret_cast<float2*>(A.part_bins)[(size_t)i * np + row] = make_float2(p.hi, p.lo);
     } else {
-      reinterpret_cast<double*>(A.part_bins)[(size_t)i * np + row] = (double)cta[i] + (double)ovf[i];
+      reinterpret_cast<double*>(A.part_bins)[(size_t)i * np + row] = hist.value(i);
     }
   }
 

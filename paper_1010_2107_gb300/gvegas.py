@@ -89,6 +89,19 @@ _SIGS = {
     "vegas_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "vegas_last_error": (ctypes.c_char_p, [_P]),
+    "vegas_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
+                                          ctypes.POINTER(_P)]),
+    "vegas_batch_destroy": (None, [_P]),
+    "vegas_batch_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result)]),
+    "vegas_batch_reset": (ctypes.c_int, [_P]),
+    "vegas_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int, _DP, _DP]),
+    "vegas_batch_get_history": (ctypes.c_int, [_P, ctypes.c_int, _DP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "vegas_batch_set_launch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "vegas_batch_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
+    "vegas_batch_profile": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
+    "vegas_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 
@@ -318,6 +331,118 @@ def vegas_microbench(op: int) -> float:
     r = ctypes.c_double()
     _check(lib().vegas_microbench(int(op), ctypes.byref(r)))
     return r.value
+
+
+class Batch:
+    """Owner of one vegas_batch handle."""
+
+    def __init__(self, handle, ndims, nbins):
+        self.handle, self.ndims, self.nbins = handle, list(ndims), int(nbins)
+
+    @property
+    def n(self):
+        return len(self.ndims)
+
+    def close(self):
+        if self.handle:
+            lib().vegas_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _bcheck(st: int, handle=None):
+    if st != OK:
+        msg = lib().vegas_batch_last_error(handle)
+        raise VegasError(st, msg.decode() if msg else "")
+
+
+def vegas_batch_create(instances, *, nbins: int = 50, seed: int = 1, precision=FP32_ACCCOMP,
+                       ybits: int = 0, alpha: float = 1.5, stream=None) -> Batch:
+    """instances: sequence of dicts with kind, ndim, params, ncall and
+    optionally instance (Philox id, default: position)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    n = len(instances)
+    cfgs = (Config * n)()
+    fns = (IntegrandDesc * n)()
+    keep = []
+    for i, ins in enumerate(instances):
+        p = np.ascontiguousarray(ins["params"], dtype=np.float64)
+        keep.append(p)
+        cfgs[i] = Config(int(ins["ndim"]), int(nbins), int(ins["ncall"]), 1, 0.0, float(alpha), 0, int(seed),
+                         int(ins.get("instance", i)), int(precision), int(ybits), _stream_handle(stream))
+        fns[i] = IntegrandDesc(int(ins["kind"]), int(ins["ndim"]), _dp(p), len(p))
+    h = _P()
+    _bcheck(lib().vegas_batch_create(n, cfgs, fns, ctypes.byref(h)))
+    return Batch(h, [ins["ndim"] for ins in instances], nbins)
+
+
+def vegas_batch_destroy(b: Batch):
+    b.close()
+
+
+def vegas_batch_iterate(b: Batch, n_iter: int, refine: bool = True, result: bool = True):
+    out = (Result * b.n)()
+    _bcheck(lib().vegas_batch_iterate(b.handle, int(n_iter), int(bool(refine)), out if result else None), b.handle)
+    return [r.as_dict() for r in out] if result else None
+
+
+def vegas_batch_reset(b: Batch):
+    _bcheck(lib().vegas_batch_reset(b.handle), b.handle)
+
+
+def vegas_batch_get_grid(b: Batch, i: int, bin_sums: bool = False):
+    d = b.ndims[i]
+    e = np.zeros((d, b.nbins + 1))
+    s = np.zeros((2, d, b.nbins)) if bin_sums else None
+    _bcheck(lib().vegas_batch_get_grid(b.handle, int(i), _dp(e), _dp(s) if bin_sums else None), b.handle)
+    return (e, s) if bin_sums else e
+
+
+def vegas_batch_get_history(b: Batch, i: int, max_iters: int = 64):
+    h = np.zeros((max_iters, 2))
+    n = ctypes.c_int()
+    _bcheck(lib().vegas_batch_get_history(b.handle, int(i), _dp(h), int(max_iters), ctypes.byref(n)), b.handle)
+    return h[:min(n.value, max_iters)]
+
+
+def vegas_batch_set_launch(b: Batch, threads: int, rounds: int):
+    _bcheck(lib().vegas_batch_set_launch(b.handle, int(threads), int(rounds)), b.handle)
+
+
+def vegas_batch_get_launch(b: Batch):
+    t, r, c, it = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().vegas_batch_get_launch(b.handle, ctypes.byref(t), ctypes.byref(r), ctypes.byref(c),
+                                         ctypes.byref(it)), b.handle)
+    return dict(threads=t.value, rounds=r.value, ctas=c.value, items=it.value)
+
+
+def vegas_batch_autotune(b: Batch):
+    t, r, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(lib().vegas_batch_autotune(b.handle, ctypes.byref(t), ctypes.byref(r), ctypes.byref(m)), b.handle)
+    return dict(threads=t.value, rounds=r.value, ms=m.value)
+
+
+def vegas_batch_profile(b: Batch, n_pass: int = 5):
+    ms = np.zeros(2)
+    _bcheck(lib().vegas_batch_profile(b.handle, int(n_pass), _dp(ms)), b.handle)
+    return dict(sample=ms[0], finalize=ms[1])
+
+
+def vegas_batch_last_error(b: Batch | None = None) -> str:
+    m = lib().vegas_batch_last_error(b.handle if b else None)
+    return m.decode() if m else ""
 
 
 def vegas_last_error(ctx: Context | None = None) -> str:
