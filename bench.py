@@ -43,10 +43,12 @@ ALGO_OPS = {
     "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),
     "rambo5": dict(philox=5 * 10 * 6, bins=20 * 6, map=20 * 3, integrand=5 * 60 + 10 * 8 + 5 * 14 + 10,
                    accumulate=20 * 2 + 14),
+    "rambo4_adjoint": dict(philox=4 * 10 * 6, bins=16 * 6, map=16 * 3,
+                           integrand=4 * 60 + 6 * 8 + 4 * 14 + 10 + 4 * 6 + 20, accumulate=5 * 7),
 }
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/); None until captured for the current kernel.
-TRAFFIC = {"dgauss8": None}
+TRAFFIC = {"dgauss8": 54272}
 
 
 def _workload(name):
@@ -174,6 +176,13 @@ def run_reference(args):
 
 
 def _config(name):
+    if name == "genz256":
+        from paper_1010_2107_gb300 import workloads as wl
+        insts = wl.genz_batch(wl.GENZ256["count"], wl.GENZ256["seed"])
+        return {"workload": name, "instances": len(insts), "ndim": "2..16", "nbins": wl.GENZ256["nbins"],
+                "ncall_total": sum(i["ncall"] for i in insts), "integrand": "genz product/corner/oscillatory",
+                "precision": wl.GENZ256["precision"], "ybits": wl.GENZ256["ybits"],
+                "iterations": wl.GENZ256["itmx"], "l2": "flushed between steps (512 MiB write)"}
     w = _workload(name)
     c = {"workload": name, "ndim": w["ndim"], "nbins": w["nbins"], "ncall": w["ncall"],
          "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw"}[w["kind"]],
@@ -181,6 +190,8 @@ def _config(name):
          "l2": "flushed between steps (512 MiB write)"}
     if w.get("mode") == "bases":
         c["iterations"] = f"{w['itmx1']}+{w['itmx2']} (BASES)"
+    elif w.get("mode") == "adjoint":
+        c["iterations"] = f"one gradient pass on the grid of {w['warmup_iters']} refining iterations"
     else:
         c["iterations"] = w.get("itmx")
     return c
@@ -189,8 +200,167 @@ def _config(name):
 # ------------------------------------------------------------------------ ours
 
 
+def _genz_ops(ins):
+    """Algorithmic FP32-pipe operations per point of one Genz instance:
+    Philox blocks, per-axis bin / map / integrand / histogram work, and the
+    per-point sums."""
+    d = ins["ndim"]
+    # bins 6 + map 3 + histogram 2, plus the family's per-axis work
+    # (product peak 3, corner peak and oscillatory 1)
+    per_axis = {1: 14, 2: 12, 3: 12}.get(ins["kind"], 14)
+    return ((d + 3) // 4) * 60 + per_axis * d + 20
+
+
+class Runner:
+    """One benchmarked workload: how to build it, run one step, time its
+    dominant kernel and run one end-to-end step through the C ABI."""
+
+    def __init__(self, name, gv, stream, rank, precision_override):
+        self.name, self.gv, self.stream, self.rank = name, gv, stream, rank
+        if name == "genz256":
+            from paper_1010_2107_gb300 import workloads as wl
+            self.w = dict(wl.GENZ256)
+            self.insts = wl.genz_batch(self.w["count"], self.w["seed"])
+            for ins in self.insts:
+                ins["instance"] = ins["instance"] + 1024 * rank
+            self.mode = "batched"
+        else:
+            self.w = _workload(name)
+            self.mode = self.w.get("mode", "vegas")
+        self.prec_name = precision_override or self.w["precision"]
+
+    def precision(self, name=None):
+        gv = self.gv
+        return {"fp32": gv.FP32_ACCCOMP, "fp32_acc64": gv.FP32_ACC64, "fp64": gv.FP64}[name or self.prec_name]
+
+    # ---------------------------------------------------------------- setup
+    def make(self, prec):
+        gv, w = self.gv, self.w
+        if self.mode == "batched":
+            h = gv.vegas_batch_create(self.insts, nbins=w["nbins"], seed=w["sample_seed"], precision=prec,
+                                      ybits=w["ybits"], stream=self.stream)
+            self.tuned = gv.vegas_batch_autotune(h)
+            return h
+        h = gv.vegas_create(w["kind"], w["ndim"], w["params"], nbins=w["nbins"], ncall=w["ncall"],
+                            nstrat=w["nstrat"], seed=w["seed"], instance=self.rank, precision=prec,
+                            ybits=w["ybits"], stream=self.stream)
+        if self.mode == "adjoint":  # the grid the gradient is taken on
+            gv.vegas_iterate(h, w["warmup_iters"], refine=True)
+        return h
+
+    @property
+    def points_per_step(self):
+        w = self.w
+        if self.mode == "batched":
+            return sum(i["ncall"] for i in self.insts) * w["itmx"]
+        if self.mode == "bases":
+            return w["ncall"] * (w["itmx1"] + w["itmx2"])
+        if self.mode == "adjoint":
+            return w["ncall"]
+        return w["ncall"] * w["itmx"]
+
+    @property
+    def launches_per_step(self):
+        w = self.w
+        if self.mode == "batched":
+            return 1 + 2 * sum(i["ndim"] for i in self.insts) + 2 * w["itmx"]
+        if self.mode == "bases":
+            return 2 + 2 + 3 * (w["itmx1"] + w["itmx2"])
+        if self.mode == "adjoint":
+            return 2
+        return 2 + 2 + 3 * w["itmx"]
+
+    def step(self, h):
+        gv, w = self.gv, self.w
+        if self.mode == "batched":
+            gv.vegas_batch_reset(h)
+            gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=False)
+        elif self.mode == "bases":
+            gv.vegas_reset_grid(h)
+            gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
+        elif self.mode == "adjoint":
+            gv.vegas_grad(h, 1000)
+        else:
+            gv.vegas_reset_grid(h)
+            gv.vegas_reset_results(h)
+            gv.vegas_iterate(h, w["itmx"], refine=True, result=False)
+
+    def result(self, h):
+        gv = self.gv
+        if self.mode == "batched":
+            res = gv.vegas_batch_iterate(h, 0)
+            return {"instances": len(res), "max_chi2_dof": max(r["chi2_dof"] for r in res),
+                    "nonfinite": sum(r["nonfinite"] for r in res)}
+        if self.mode == "adjoint":
+            g, I = gv.vegas_grad(h, 1000)
+            return {"I": I, "dI_dM": g[0], "dI_dGamma": g[1], "dI_dT": g[2]}
+        r = gv.vegas_iterate(h, 0, refine=False)
+        return {"I": r["I"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"], "nonfinite": r["nonfinite"]}
+
+    # --------------------------------------------------- kernel-level timing
+    def kernel_ms(self, h):
+        """(dominant kernel name, ms per launch, points per launch, other timings)."""
+        gv = self.gv
+        if self.mode == "batched":
+            p = gv.vegas_batch_profile(h, 5)
+            return "k_batch_sample", p["sample"], sum(i["ncall"] for i in self.insts), {"finalize_ms": p["finalize"]}
+        if self.mode == "adjoint":
+            import torch
+            gv.vegas_grad(h, 1000)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            for _ in range(5):
+                gv.vegas_grad(h, 1000)
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            return "k_grad", a.elapsed_time(b) / 5, self.w["ncall"], {}
+        p = gv.vegas_profile_pass(h, 20)
+        return "k_sample", p["sample"], self.w["ncall"], {"reduce_ms": p["reduce"], "finalize_ms": p["finalize"]}
+
+    def ops_per_point(self):
+        if self.mode == "batched":
+            tot = sum(i["ncall"] for i in self.insts)
+            return sum(_genz_ops(i) * i["ncall"] for i in self.insts) / tot
+        ops = ALGO_OPS.get(self.name)
+        return sum(ops.values()) if ops else None
+
+    def launch(self, h):
+        gv = self.gv
+        if self.mode == "batched":
+            return gv.vegas_batch_get_launch(h)
+        return gv.vegas_get_launch(h)
+
+    # ------------------------------------------------------------ end to end
+    def e2e_step(self, h):
+        """One step through the public API with host buffers: inputs uploaded
+        from host memory, the result read back; returns (h2d, d2h) bytes."""
+        import numpy as np
+        gv, w = self.gv, self.w
+        if self.mode == "batched":
+            gv.vegas_batch_reset(h)
+            gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=True)
+            return 0, 48 * len(self.insts) + 1200 * len(self.insts)
+        d, N = w["ndim"], w["nbins"]
+        edges0 = np.tile(np.arange(N + 1, dtype=np.float64) / N, (d, 1))
+        gv.vegas_set_grid(h, edges0)
+        gv.vegas_set_params(h, np.asarray(w["params"], dtype=np.float64))
+        h2d = edges0.nbytes + 8 * (3 * 32 + 24)
+        if self.mode == "bases":
+            gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0)
+            return h2d, 160
+        if self.mode == "adjoint":
+            gv.vegas_grad(h, 1000)
+            return h2d, 8 * 5
+        gv.vegas_reset_results(h)
+        gv.vegas_iterate(h, w["itmx"], refine=True)
+        return h2d, 160
+
+    def close(self, h):
+        h.close()
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_1010_2107_gb300 import _build
@@ -201,38 +371,18 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
     torch.cuda.set_device(local)
     _build.build()
-    name = args.workload
-    w = _workload(name)
-    d, N, ncall = w["ndim"], w["nbins"], w["ncall"]
-    bases = w.get("mode") == "bases"
-    iters = (w["itmx1"] + w["itmx2"]) if bases else w["itmx"]
-    points_per_step = ncall * iters
     # A dedicated stream: the library orders its work on it and the events
     # below are recorded on it (torch's default stream has handle 0, which
     # the library would replace by a stream of its own).
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    prec = {"fp32": gv.FP32_ACCCOMP, "fp32_acc64": gv.FP32_ACC64, "fp64": gv.FP64}[args.precision or w["precision"]]
-
-    def make(precision):
-        return gv.vegas_create(w["kind"], d, w["params"], nbins=N, ncall=ncall, nstrat=w["nstrat"],
-                               seed=w["seed"], instance=rank, precision=precision, ybits=w["ybits"],
-                               stream=stream)
-
-    def step(ctx):
-        gv.vegas_reset_grid(ctx)
-        if bases:
-            gv.bases_integrate(ctx, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
-        else:
-            gv.vegas_reset_results(ctx)
-            gv.vegas_iterate(ctx, w["itmx"], refine=True, result=False)
-
-    launches_per_step = 2 + (2 if bases else 2) + 3 * iters
+    R = Runner(args.workload, gv, stream, rank, args.precision)
+    prec = R.precision()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def timed(ctx, k, warm):
+    def timed(h, k, warm):
         for _ in range(warm):
-            step(ctx)
+            R.step(h)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -241,89 +391,83 @@ def run_ours(args):
         for a, b in evs:
             flush.zero_()
             a.record(stream)
-            step(ctx)
+            R.step(h)
             b.record(stream)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         return [a.elapsed_time(b) for a, b in evs]
 
-    ctx = make(prec)
+    h = R.make(prec)
     with ClockSampler(local) as clk:
-        step_ms = timed(ctx, args.steps, args.warmup)
+        step_ms = timed(h, args.steps, args.warmup)
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * points_per_step * args.steps / (total_ms / 1e3)
-    res = gv.vegas_iterate(ctx, 0, refine=False)  # result of the last step (reads back)
+    pps = R.points_per_step
+    value = world * pps * args.steps / (total_ms / 1e3)
+    res = R.result(h)
 
-    # kernel-level timing on the launching stream: roofline of the sampling kernel
+    # roofline of the dominant kernel, timed by CUDA events on its stream
     peaks, peak_src = _measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    prof = gv.vegas_profile_pass(ctx, 20)
-    launch = gv.vegas_get_launch(ctx)
-    ops = ALGO_OPS.get(name)
+    kname, kms, units, other = R.kernel_ms(h)
+    ops_pt = R.ops_per_point()
     roof = None
-    if ops:
-        ops_pt = sum(ops.values())
-        achieved = ops_pt * ncall / (prof["sample"] * 1e-3) / 1e12
-        peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        tr = TRAFFIC.get(name)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": tr,
-                "kernel": "k_sample", "ops_per_point": ops_pt, "ms_per_launch": prof["sample"],
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
-                              f"({peak_src} max clock)"}
-    red_bytes = 8 * (2 * d * N + 5) * launch["ctas"] + 8 * (2 * d * N + 5)
-    reduction = {"kernel": "k_reduce", "bytes_per_launch": red_bytes, "ms_per_launch": prof["reduce"],
-                 "achieved_gbs": red_bytes / (prof["reduce"] * 1e-3) / 1e9,
-                 "peak_gbs": peaks.get("hbm_gbs"), "finalize_ms": prof["finalize"]}
+    if ops_pt:
+        achieved = ops_pt * units / (kms * 1e-3) / 1e12
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * 128 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get(args.workload), "kernel": kname, "ops_per_point": round(ops_pt, 1),
+                "points_per_launch": units, "ms_per_launch": kms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)"}
+        if prec == gv.FP64:
+            roof["note"] = "FP64 form: bound by the FP64 pipe, see fp64_rate"
+    extra = dict(other)
+    if R.mode in ("bases", "vegas"):
+        launch = gv.vegas_get_launch(h)
+        d, N = R.w["ndim"], R.w["nbins"]
+        red_bytes = 8 * (2 * d * N + 5) * launch["ctas"] + 8 * (2 * d * N + 5)
+        extra = {"reduction": {"kernel": "k_reduce", "bytes_per_launch": red_bytes,
+                               "ms_per_launch": other["reduce_ms"],
+                               "achieved_gbs": red_bytes / (other["reduce_ms"] * 1e-3) / 1e9,
+                               "peak_gbs": peaks.get("hbm_gbs")},
+                 "finalize_ms": other["finalize_ms"]}
 
-    # plain FP64 GPU path on the same points (speed-up denominator)
+    # the plain FP64 GPU path on the same points (speed-up denominator)
     fp64 = None
     if not args.no_fp64 and prec != gv.FP64:
-        c64 = make(gv.FP64)
+        h64 = R.make(gv.FP64)
         k64 = max(3, args.steps // 4)
-        ms64 = timed(c64, k64, 2)
-        r64 = gv.vegas_iterate(c64, 0, refine=False)
-        fp64 = {"value": points_per_step * k64 / (sum(ms64) / 1e3), "unit": UNIT, "steps": k64,
-                "I": r64["I"], "sigma": r64["sigma"],
-                "sample_kernel_ms": gv.vegas_profile_pass(c64, 5)["sample"]}
+        ms64 = timed(h64, k64, 2)
+        fp64 = {"value": pps * k64 / (sum(ms64) / 1e3), "unit": UNIT, "steps": k64, "result": R.result(h64)}
         fp64["speedup"] = (value / world) / fp64["value"]
-        c64.close()
+        R.close(h64)
 
-    # end to end through the C ABI with host buffers: grid and parameters
-    # uploaded from host memory, the result read back, every step.
-    edges0 = np.tile(np.arange(N + 1, dtype=np.float64) / N, (d, 1))
-    params = np.asarray(w["params"], dtype=np.float64)
+    # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    t0 = time.perf_counter()
     ke = max(3, args.steps // 2)
+    t0 = time.perf_counter()
     for _ in range(ke):
-        gv.vegas_set_grid(ctx, edges0)
-        gv.vegas_set_params(ctx, params)
-        if bases:
-            out, _ = gv.bases_integrate(ctx, w["itmx1"], 0.0, w["itmx2"], 0.0)
-        else:
-            gv.vegas_reset_results(ctx)
-            out = gv.vegas_iterate(ctx, w["itmx"], refine=True)
+        h2d, d2h = R.e2e_step(h)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * points_per_step * ke / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": edges0.nbytes + 8 * (2 * 32 + 16),
-           "d2h_bytes_per_step": 160, "steps": ke}
+    e2e = {"value": world * pps * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": ke}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        rate, n, dt = oracle_rate(name, 3, 3) if bases else oracle_rate(name, 1, 0)
+    if rank == 0 and world == 1 and not args.no_cpu and R.mode in ("bases", "vegas"):
+        bases = R.mode == "bases"
+        rate, n, dt = oracle_rate(args.workload, 3, 3) if bases else oracle_rate(args.workload, 1, 0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} points: full-NCALL iterations of the same workload "
                          f"({'3+3 BASES' if bases else '1 VEGAS'}), {dt:.1f} s single-threaded FP64 C oracle"}
@@ -334,16 +478,17 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != gv.FP64 else "f64",
-            "data": "synthetic", "config": dict(_config(name), accumulation=args.precision or w["precision"],
-                                                launch=launch),
-            "roofline": roof, "reduction": reduction, "fp64_path": fp64, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
-            "result": {"I": res["I"], "sigma": res["sigma"], "chi2_dof": res["chi2_dof"],
-                       "nonfinite": res["nonfinite"]},
+            "data": "synthetic", "config": dict(_config(args.workload), accumulation=R.prec_name,
+                                                launch=R.launch(h)),
+            "roofline": roof, **extra, "fp64_path": fp64, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": R.launches_per_step * args.steps, "clocks": clocks,
+            "result": res,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         }
+        if R.mode == "batched":
+            line["config"]["autotuned"] = R.tuned
         print(json.dumps(line))
-    ctx.close()
+    R.close(h)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -380,7 +525,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dgauss8", choices=["dgauss8", "gauss4", "rambo5"])
+    ap.add_argument("--workload", default="dgauss8",
+                    choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
