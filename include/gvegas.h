@@ -231,11 +231,22 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
                                double* x, double* jac, double* f);
 
 /* Launch shape of the sampling kernel: threads per CTA (multiple of 32,
- * 64..1024) and CTAs per SM (0 = as many as fit).  Used by the autotuner;
- * takes effect on the next iteration. */
+ * 64..256) and CTAs per SM (0 = as many as fit).  Used by the autotuner;
+ * takes effect on the next iteration.  EINVAL outside those ranges. */
 vegas_status vegas_set_launch(vegas_ctx* ctx, int threads, int ctas_per_sm);
 vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
                               int* ctas_per_sm);
+
+/* Histogram tile of the sampling kernel (no counterpart in the paper, whose
+ * host code sums the bins): each thread evaluates `points_per_thread`
+ * points (1..8; 0 = automatic) between two gathers of the CTA's
+ * (axis, bin) buckets.  Changes only speed and the summation order inside
+ * a CTA, never which points are drawn.  get_tile returns the points per
+ * thread and the bucket capacity per (axis, bin) in use.  EINVAL outside
+ * the range or when the tile does not fit in shared memory (the previous
+ * shape then stays). */
+vegas_status vegas_set_tile(vegas_ctx* ctx, int points_per_thread);
+vegas_status vegas_get_tile(vegas_ctx* ctx, int* points_per_thread, int* cap);
 
 /* Measurement (the paper times whole programs, Sec. 3.3; this times each
  * kernel): runs n_pass evaluation passes at the current iteration index

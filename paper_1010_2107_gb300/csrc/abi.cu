@@ -50,6 +50,7 @@ struct vegas_ctx {
   // launch geometry
   int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, lanes_req = 0, occ = 0;
   int cap = 16;  // histogram bucket capacity (see sample_kernel.cuh)
+  int ppt = 1, ppt_req = 0;  // points per thread per histogram tile
   size_t smem = 0;
   // device buffers
   double* d_edges = nullptr;
@@ -134,39 +135,38 @@ void destroy_graphs(vegas_ctx* c) {
 // (or as requested), capped by the work available.
 vegas_status configure_launch(vegas_ctx* c) {
   const int d = c->cfg.ndim, N = c->cfg.nbins;
-  // Bucket capacity per (axis, bin) and tile: about 2.5x the mean fill of a
-  // uniformly spread tile plus 4, a power of two in 4..64; halved until the
-  // CTA's shared memory fits.
-  int cap = 4;
-  while (cap < 64 && cap < (5 * c->threads) / (2 * N) + 4) cap *= 2;
-  int occ = 0;
-  for (;;) {
-    c->smem = c->ke.smem(d, N, cap);
-    cudaError_t e = cudaSuccess;
-    occ = 0;
-    if (c->smem <= 227 * 1024) {
-      e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->ke.sample, c->threads, c->smem);
-    }
-    if (e != cudaSuccess)
-      return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
-    if (occ >= 1 || cap == 1) break;
-    cap /= 2;
-  }
-  c->cap = cap;
-  if (occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %zu B smem",
-                              c->threads, c->smem);
+  // Histogram tile (gv::choose_tile): points per thread between gathers and
+  // bucket capacity, against the CTAs per SM each leaves resident.
+  cudaError_t e = cudaSuccess;
+  auto occ_of = [&](int cap, int) -> int {
+    const size_t smem = c->ke.smem(d, N, cap);
+    int o = 0;
+    if (e != cudaSuccess || smem > 227 * 1024) return 0;
+    e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, c->ke.sample, c->threads, smem);
+    return e == cudaSuccess ? o : 0;
+  };
+  int occ_cap = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c->ke.sample, c->threads, 0);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+  const gv::TileShape t = gv::choose_tile(c->threads, N, c->ppt_req, occ_cap, occ_of);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+  if (t.occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %d points per thread",
+                                c->threads, t.ppt);
+  // leave the attribute at the chosen size
+  c->smem = c->ke.smem(d, N, t.cap);
+  e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+  c->cap = t.cap;
+  c->ppt = t.ppt;
+  const int occ = t.occ;
   c->occ = occ;
   const int per_sm = c->ctas_per_sm_req > 0 ? std::min(c->ctas_per_sm_req, occ) : occ;
   const int64_t cap_ctas = (int64_t)c->sm_count * per_sm;
-  const int64_t cap_threads = cap_ctas * c->threads;
   uint64_t units;
   if (c->strat) {
-    // lanes per hypercube: enough groups for >= 4 rounds of the resident
-    // threads (load balance), at most 32 and at most the points per cube
-    int L = 1;
-    while (L < 32 && (uint64_t)(2 * L) <= c->nc && c->ncubes * (uint64_t)L < 4 * (uint64_t)cap_threads) L *= 2;
+    // lanes per hypercube: the best balance of rounds and chain length
+    int L = gv::choose_lanes(c->ncubes, c->nc, c->threads, cap_ctas);
     if (c->lanes_req > 0) L = std::min<int>(c->lanes_req, (int)std::min<uint64_t>(32, c->nc));
     int Lp = 1;
     while (2 * Lp <= L) Lp *= 2;
@@ -200,9 +200,11 @@ gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
   A.ybits = c->ybits;
   A.lanes = c->lanes;
   A.cap = c->cap;
+  A.ppt = c->ppt;
   A.strat = c->strat;
   A.key0 = (uint32_t)c->cfg.seed;
   A.key1 = (uint32_t)(c->cfg.seed >> 32);
+  gv::philox_key_schedule(A.key0, A.key1, A.ks);
   A.instance = c->cfg.instance;
   A.it_override = it_override;
   A.ncall = (uint64_t)c->cfg.ncall;
@@ -461,6 +463,11 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e)));
+  e = gv_prepare_aux_kernels();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
   } else {
@@ -762,6 +769,28 @@ vegas_status vegas_set_launch(vegas_ctx* c, int threads, int ctas_per_sm) {
   return st;
 }
 
+vegas_status vegas_set_tile(vegas_ctx* c, int points_per_thread) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (points_per_thread < 0 || points_per_thread > 8)
+    return c->fail(VEGAS_EINVAL, "points_per_thread must be in 0..8 (0: automatic)");
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int p0 = c->ppt_req;
+  c->ppt_req = points_per_thread;
+  vegas_status st = configure_launch(c);
+  if (st) {
+    c->ppt_req = p0;
+    configure_launch(c);
+  }
+  return st;
+}
+
+vegas_status vegas_get_tile(vegas_ctx* c, int* points_per_thread, int* cap) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (points_per_thread) *points_per_thread = c->ppt;
+  if (cap) *cap = c->cap;
+  return VEGAS_OK;
+}
+
 vegas_status vegas_get_launch(vegas_ctx* c, int* threads, int* ctas, int* ctas_per_sm) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
   if (threads) *threads = c->threads;
@@ -964,22 +993,23 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   // Launch shape (as for a context) with the CTA count bounded by the rows
   // of partial sums that fit in the scratch array.
   const int threads = 256;
-  int cap = 4;
-  while (cap < 64 && cap < (5 * threads) / (2 * N) + 4) cap *= 2;
-  int occ = 0;
-  size_t smem = 0;
-  for (;;) {
-    smem = ke.smem(d, N, cap);
-    occ = 0;
-    if (smem <= 227 * 1024) {
-      e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke.sample, threads, smem);
-      if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
-    }
-    if (occ >= 1 || cap == 1) break;
-    cap /= 2;
-  }
-  if (occ < 1) return thread_fail(VEGAS_EINVAL, "sampling kernel does not fit in shared memory");
+  auto occ_of = [&](int cap, int) -> int {
+    const size_t sm = ke.smem(d, N, cap);
+    int o = 0;
+    if (e != cudaSuccess || sm > 227 * 1024) return 0;
+    e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ke.sample, threads, sm);
+    return e == cudaSuccess ? o : 0;
+  };
+  int occ_cap = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, ke.sample, threads, 0);
+  const gv::TileShape t = e == cudaSuccess ? gv::choose_tile(threads, N, 0, occ_cap, occ_of) : gv::TileShape{1, 4, 0};
+  if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+  if (t.occ < 1) return thread_fail(VEGAS_EINVAL, "sampling kernel does not fit in shared memory");
+  const int ppt = t.ppt, cap = t.cap, occ = t.occ;
+  const size_t smem = ke.smem(d, N, cap);
+  e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   const int dN = d * N;
   const size_t off_st = 0;
   const size_t off_dp = align256(off_st + sizeof(GState));
@@ -998,7 +1028,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   int L = 1;
   uint64_t units = (uint64_t)cfg->ncall;
   if (strat) {
-    while (L < 32 && (uint64_t)(2 * L) <= nc && G * (uint64_t)L < 4 * (uint64_t)(cap_ctas * threads)) L *= 2;
+    L = gv::choose_lanes(G, nc, threads, std::min<int64_t>(cap_ctas, max_rows));
     units = G * (uint64_t)L;
   }
   const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)((units + threads - 1) / threads), cap_ctas, max_rows}));
@@ -1027,9 +1057,11 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   A.ybits = ybits;
   A.lanes = L;
   A.cap = cap;
+  A.ppt = ppt;
   A.strat = strat;
   A.key0 = (uint32_t)cfg->seed;
   A.key1 = (uint32_t)(cfg->seed >> 32);
+  gv::philox_key_schedule(A.key0, A.key1, A.ks);
   A.instance = cfg->instance;
   A.it_override = (int)it;
   A.ncall = (uint64_t)cfg->ncall;

@@ -61,8 +61,9 @@ struct BatchState {
 };
 
 struct BatchArgs {
-  int n, nitems, N, cap;
+  int n, nitems, N, cap, ppt;
   uint32_t key0, key1;
+  uint32_t ks[kPhiloxKeyWords];  // Philox round keys of (key0, key1)
   const BatchInst* inst;
   const BatchItem* items;
   const void* tab;        // float2 (FP32 form) or double2 (FP64) cells
@@ -125,6 +126,8 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   A.g_log2 = 0;
   A.key0 = B.key0;
   A.key1 = B.key1;
+#pragma unroll
+  for (int i = 0; i < kPhiloxKeyWords; ++i) A.ks[i] = B.ks[i];
   A.inv_gb_d = 1.0 / (double)(1ull << YB);
   A.inv_gb_f = (float)A.inv_gb_d;
   int cd[DM];
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
       for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)dp[i];
       cur = W.inst;
     }
-    hist.bind(smem + L::hist(N), dN, N, B.cap);
+    hist.bind(smem + L::hist(N), dN, N, B.cap, B.ppt);
     hist.zero(tid, blockDim.x);
     __syncthreads();
     A.d = d;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
         sw2.add(wh * wh);
         hist.template scatter<DM>(kb, d, wh);
       }
-      hist.gather(tid, blockDim.x);
+      if ((r + 1) % (uint32_t)B.ppt == 0 || r + 1 == rounds) hist.gather(tid, blockDim.x);
     }
     // the item's partial row: cells, then sum w, sum w^2, non-finite count
     for (int i = tid; i < 2 * dN; i += blockDim.x) {
@@ -268,7 +271,8 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
     return;
   }
   const int i = b - B.naxes;
-  if (i >= B.n || threadIdx.x != 0) return;
+  if (i >= B.n || threadIdx.x >= 32) return;  // one warp per instance; lane 0 writes
+  const bool w0 = threadIdx.x == 0;
   const BatchInst I = B.inst[i];
   const int dN = I.d * B.N;
   const double sw = row_sum(B, I, 2 * dN), sw2 = row_sum(B, I, 2 * dN + 1);
@@ -278,19 +282,33 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
   double var = (sw2 / n - Ij * Ij) / (n - 1.0);
   if (var < 0.0) var = 0.0;
   BatchState* st = B.st + i;
-  st->last_I = Ij;
-  st->last_var = var;
+  if (w0) {
+    st->last_I = Ij;
+    st->last_var = var;
+  }
   if (!B.record) return;
   int h = st->nhist;
   if (h < kBatchHist) {
-    st->hist[h][0] = Ij;
-    st->hist[h][1] = var;
-    st->nhist = ++h;
+    if (w0) {
+      st->hist[h][0] = Ij;
+      st->hist[h][1] = var;
+      st->nhist = h + 1;
+    }
+    ++h;
   }
-  st->nonfinite += (long long)nf;
-  st->samples += (long long)I.ncall;
-  st->it += 1;
-  combine_history(st->hist, h, &st->I, &st->sigma, &st->chi2);
+  __syncwarp();
+  if (w0) {
+    st->nonfinite += (long long)nf;
+    st->samples += (long long)I.ncall;
+    st->it += 1;
+  }
+  double Ib, sg, chi;
+  combine_history(st->hist, h, &Ib, &sg, &chi);
+  if (w0) {
+    st->I = Ib;
+    st->sigma = sg;
+    st->chi2 = chi;
+  }
 }
 
 __global__ void k_batch_reset(BatchState* st, int n, int reset_counter) {
@@ -325,7 +343,7 @@ struct vegas_batch {
   std::vector<double> derived;  // [n][kNumDerived]
   int sm_count = 0;
   // launch shape
-  int threads = 256, rounds = 32, ctas = 0, cap = 16, occ = 0;
+  int threads = 256, rounds = 32, ctas = 0, cap = 16, ppt = 1, occ = 0;
   size_t smem = 0;
   const void* kernel = nullptr;
   // host copies of the tables
@@ -449,22 +467,28 @@ vegas_status build_items(vegas_batch* b) {
 
 vegas_status configure(vegas_batch* b) {
   b->kernel = pick_batch_kernel(b->prec, b->ybits);
-  int cap = 4;
-  while (cap < 64 && cap < (5 * b->threads) / (2 * b->N) + 4) cap *= 2;
-  int occ = 0;
-  for (;;) {
-    b->smem = batch_smem(b->prec, b->N, cap);
-    occ = 0;
-    if (b->smem <= 227 * 1024) {
-      BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-      BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->kernel, b->threads, b->smem));
-    }
-    if (occ >= 1 || cap == 1) break;
-    cap /= 2;
-  }
-  if (occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
-  b->cap = cap;
-  b->occ = occ;
+  BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared));
+  cudaError_t e = cudaSuccess;
+  auto occ_of = [&](int cap, int) -> int {
+    const size_t smem = batch_smem(b->prec, b->N, cap);
+    int o = 0;
+    if (e != cudaSuccess || smem > 227 * 1024) return 0;
+    e = cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, b->kernel, b->threads, smem);
+    return e == cudaSuccess ? o : 0;
+  };
+  int occ_cap = 0;
+  BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, b->kernel, b->threads, 0));
+  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, occ_cap, occ_of);
+  BK(b, e);
+  if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
+  b->smem = batch_smem(b->prec, b->N, t.cap);
+  BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  b->cap = t.cap;
+  b->ppt = t.ppt;
+  b->occ = t.occ;
+  const int occ = t.occ;
   b->ctas = b->sm_count * occ;
   return build_items(b);
 }
@@ -475,8 +499,10 @@ BatchArgs batch_args(const vegas_batch* b, int refine, int record) {
   A.nitems = (int)b->items.size();
   A.N = b->N;
   A.cap = b->cap;
+  A.ppt = b->ppt;
   A.key0 = (uint32_t)b->seed;
   A.key1 = (uint32_t)(b->seed >> 32);
+  gv::philox_key_schedule(A.key0, A.key1, A.ks);
   A.inst = b->d_inst;
   A.items = b->d_items;
   A.tab = b->prec == VG_FP64 ? (const void*)b->d_tab64 : (const void*)b->d_tab32;
@@ -615,6 +641,16 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
     b->fail(VEGAS_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    return bail(VEGAS_ECUDA);
+  }
+  // one shared-memory split for every kernel of the iteration (no SM
+  // repartitioning between them)
+  e = gv_prepare_aux_kernels();
+  for (const void* f : {(const void*)gv::k_batch_finalize, (const void*)gv::k_batch_reset})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) {
+    b->fail(VEGAS_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
     return bail(VEGAS_ECUDA);
   }
   if (c0.stream) {

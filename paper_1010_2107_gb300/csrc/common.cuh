@@ -40,6 +40,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// Round keys of Philox4x32-10 for key (k0, k1): ks[2 r], ks[2 r + 1] are
+// the two key words of round r (Weyl increments 0x9E3779B9, 0xBB67AE85).
+// Kernels receive them precomputed in their arguments, so every round reads
+// its key from the constant bank instead of adding it on the fly.
+constexpr int kPhiloxKeyWords = 20;
+__host__ __device__ inline void philox_key_schedule(uint32_t k0, uint32_t k1, uint32_t* ks) {
+  for (int r = 0; r < 10; ++r) {
+    ks[2 * r] = k0;
+    ks[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t (&ks)[kPhiloxKeyWords]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ ks[2 * r], lo1, hi0 ^ c.w ^ ks[2 * r + 1], lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint32_t pick(const uint4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
@@ -135,8 +161,10 @@ struct SampleArgs {
   int d, N, g, ybits;
   int lanes;               // lanes per hypercube (stratified mode), power of two <= 32
   int cap;                 // bucket capacity per (axis, bin) and tile
+  int ppt;                 // points per thread per tile (>= 1)
   int strat;
   uint32_t key0, key1, instance;
+  uint32_t ks[kPhiloxKeyWords];  // Philox round keys of (key0, key1)
   int it_override;         // >= 0: use this iteration index
   uint64_t ncall;
   uint32_t nc;             // points per hypercube

@@ -29,7 +29,16 @@ __global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
     // compensated FP32 pairs: fixed-order compensated sum, one conversion
     const float2* p = reinterpret_cast<const float2*>(F.part_bins) + (size_t)col * np;
     fpair acc{0.f, 0.f};
-    for (int r = lane; r < np; r += 32) {
+    int r = lane;
+    // eight loads in flight per lane, merged in row order
+    for (; r + 7 * 32 < np; r += 8 * 32) {
+      float2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = p[r + 32 * j];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) comp_merge(acc, fpair{v[j].x, v[j].y});
+    }
+    for (; r < np; r += 32) {
       const float2 v = p[r];
       comp_merge(acc, fpair{v.x, v.y});
     }
@@ -57,7 +66,15 @@ __global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
     return;
   }
   double acc = 0.0;
-  for (int r = lane; r < np; r += 32) acc += src[r];
+  int r = lane;
+  for (; r + 7 * 32 < np; r += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = src[r + 32 * j];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc += v[j];
+  }
+  for (; r < np; r += 32) acc += src[r];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if (lane == 0) *dst = acc * sc;
@@ -69,9 +86,11 @@ __device__ void refine_axis(const FinArgs& F, int a) {
                    F.tab64 + (size_t)a * N, F.tab32 + (size_t)a * N, N, F.alpha);
 }
 
+// Step 6 for the pass, by one full warp (lane 0 writes the state).
 __device__ void record_iteration(const FinArgs& F) {
   GState* st = F.st;
   const double* t = F.tot;
+  const int lane = threadIdx.x & 31;
   double I, var;
   if (F.strat) {
     const double G = (double)F.ncubes;
@@ -83,30 +102,40 @@ __device__ void record_iteration(const FinArgs& F) {
     var = (t[TOT_SW2] / n - I * I) / (n - 1.0);
     if (var < 0.0) var = 0.0;
   }
-  st->last_I = I;
-  st->last_var = var;
-  st->last_sw = t[TOT_SW];
-  st->last_sw2 = t[TOT_SW2];
-  st->last_nonfinite = (long long)t[TOT_NONFINITE];
+  if (lane == 0) {
+    st->last_I = I;
+    st->last_var = var;
+    st->last_sw = t[TOT_SW];
+    st->last_sw2 = t[TOT_SW2];
+    st->last_nonfinite = (long long)t[TOT_NONFINITE];
+  }
   if (!F.record) return;
   int h = st->nhist;
   if (h < kMaxHist) {
-    st->hist[h][0] = I;
-    st->hist[h][1] = var;
-    st->nhist = ++h;
+    if (lane == 0) {
+      st->hist[h][0] = I;
+      st->hist[h][1] = var;
+      st->nhist = h + 1;
+    }
+    ++h;
   }
-  st->nonfinite += (long long)t[TOT_NONFINITE];
-  st->samples += (long long)F.ncall;
-  st->it += 1;
+  __syncwarp();
+  if (lane == 0) {
+    st->nonfinite += (long long)t[TOT_NONFINITE];
+    st->samples += (long long)F.ncall;
+    st->it += 1;
+  }
   // Inverse-variance combination over the window (Lepage).
   double Ib, sg, chi;
   combine_history(st->hist, h, &Ib, &sg, &chi);
-  st->I = Ib;
-  st->sigma = sg;
-  st->chi2 = chi;
-  if (st->acc > 0.0 && sg < st->acc * fabs(Ib)) {
-    st->done = 1;
-    st->stopped = 1;
+  if (lane == 0) {
+    st->I = Ib;
+    st->sigma = sg;
+    st->chi2 = chi;
+    if (st->acc > 0.0 && sg < st->acc * fabs(Ib)) {
+      st->done = 1;
+      st->stopped = 1;
+    }
   }
 }
 
@@ -116,7 +145,7 @@ __global__ void __launch_bounds__(256) k_finalize(const FinArgs F) {
   if (!F.st->live) return;
   if ((int)blockIdx.x < F.d) {
     if (F.refine) refine_axis(F, blockIdx.x);
-  } else if (threadIdx.x == 0) {
+  } else if (threadIdx.x < 32) {
     record_iteration(F);
   }
 }
@@ -178,6 +207,20 @@ __global__ void k_tables(const double* edges, int d, int N, double2* tab64, floa
 }  // namespace gv
 
 extern "C" {
+
+// The sampling kernels run with most of the unified L1 / shared memory as
+// shared memory; the small kernels between them ask for the same split, so
+// that an SM need not change its partition (and drain) at every boundary.
+cudaError_t gv_prepare_aux_kernels(void) {
+  const void* fns[] = {(const void*)gv::k_reduce, (const void*)gv::k_finalize, (const void*)gv::k_colsum,
+                       (const void*)gv::k_control, (const void*)gv::k_uniform_grid, (const void*)gv::k_tables};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s) {
   const int cols = 2 * F->d * F->N + 5;

@@ -47,6 +47,72 @@ bool entries_rambo_y53(int prec, int d, KernelEntry* out);
 int expected_nparams(int kind, int d);
 bool derive_params(int kind, int d, const double* p, double* dv, double* scale, std::string* why);
 
+// Histogram tile of a sampling kernel: ppt points per thread between two
+// gathers, bucket capacity cap per (axis, bin), and the CTAs per SM that
+// leaves resident.
+struct TileShape {
+  int ppt, cap, occ;
+};
+
+// Choice of the tile for `threads` threads over N bins.  A tile of
+// threads x ppt points fills a cell with m = threads ppt / N points on
+// average; the capacity runs from m + 4 sqrt(m) + 2 (a Poisson tail: claims
+// past it are rare and spill to float atomics) down to m + 2 sqrt(m) + 1,
+// in steps of 4, until the CTAs per SM reach occ_cap (the bound without
+// shared memory).  Larger tiles amortise the gather and its barriers, so
+// the largest ppt in {4, 2, 1} that keeps at least 16 warps per SM (or the
+// most the kernel can have) wins; ppt_req > 0 forces the tile and then halves
+// the capacity until it fits.  occ_of(cap, ppt) returns the CTAs per SM (0:
+// does not fit).
+template <class OccOf>
+inline TileShape choose_tile(int threads, int N, int ppt_req, int occ_cap, OccOf occ_of) {
+  auto ceil4 = [](double v) { return ((int)v + 1 + 3) & ~3; };
+  TileShape best{0, 0, 0};
+  const int wanted = occ_cap * threads / 32 < 16 ? occ_cap * threads / 32 : 16;
+  const int cands[3] = {4, 2, 1};
+  for (int i = 0; i < 3; ++i) {
+    const int ppt = ppt_req > 0 ? ppt_req : cands[i];
+    const double m = (double)threads * ppt / N;
+    int hi = ceil4(m + 4.0 * __builtin_sqrt(m) + 2.0), lo = ceil4(m + 2.0 * __builtin_sqrt(m) + 1.0);
+    hi = hi > 64 ? 64 : hi;
+    lo = lo > hi ? hi : lo;
+    TileShape t{ppt, hi, 0};
+    for (int cap = hi; cap >= lo; cap -= 4) {
+      const int o = occ_of(cap, ppt);
+      if (o > t.occ) t = TileShape{ppt, cap, o};
+      if (o >= occ_cap) break;
+    }
+    if (ppt_req > 0) {  // forced tile: shrink the capacity until it fits
+      for (int cap = lo; t.occ < 1 && cap > 4;) {
+        cap = cap / 2 < 4 ? 4 : cap / 2;
+        const int o = occ_of(cap, ppt);
+        if (o > 0) t = TileShape{ppt, cap, o};
+      }
+      return t;
+    }
+    if (t.occ * threads / 32 >= wanted) return t;
+    if (t.occ > best.occ) best = t;
+  }
+  if (best.occ > 0) return best;
+  // nothing fits at the smallest tile's capacities: halve below them
+  for (int cap = 8; cap >= 4; cap /= 2) {
+    const int o = occ_of(cap, 1);
+    if (o > 0) return TileShape{1, cap, o};
+  }
+  return TileShape{1, 4, 0};
+}
+
+// Lanes per hypercube (stratified sampling): the smallest power of two L
+// <= min(32, nc) that gives at least four rounds of `ctas` CTAs of
+// `threads` threads over the G hypercubes (load balance).  Larger L would
+// shorten the last round, but it also packs more points of one hypercube
+// into a histogram tile, which crowds its (axis, bin) buckets.
+inline int choose_lanes(uint64_t G, uint64_t nc, int threads, int64_t ctas) {
+  int L = 1;
+  while (L < 32 && (uint64_t)(2 * L) <= nc && G * (uint64_t)L < 4 * (uint64_t)ctas * (uint64_t)threads) L *= 2;
+  return L;
+}
+
 // Arguments of the per-sample dump kernel.
 struct DumpArgs {
   SampleArgs S;
@@ -62,6 +128,7 @@ struct DumpArgs {
 }  // namespace gv
 
 extern "C" {
+cudaError_t gv_prepare_aux_kernels(void);
 cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);

@@ -126,13 +126,13 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
     if (a < d) {
       uint64_t m;
       if (YB == 24) {
-        if ((a & 3) == 0) w4 = philox4x32_10(make_uint4(s, (uint32_t)(a >> 2), it, A.instance), A.key0, A.key1);
+        if ((a & 3) == 0) w4 = philox4x32_10(make_uint4(s, (uint32_t)(a >> 2), it, A.instance), A.ks);
         const uint32_t u = pick(w4, a & 3);
         if (words_out) words_out[a] = u;
         m = u >> 8;
       } else {
         if (((2 * a) & 3) == 0)
-          w4 = philox4x32_10(make_uint4(s, (uint32_t)((2 * a) >> 2), it, A.instance), A.key0, A.key1);
+          w4 = philox4x32_10(make_uint4(s, (uint32_t)((2 * a) >> 2), it, A.instance), A.ks);
         const uint32_t uh = pick(w4, (2 * a) & 3), ul = pick(w4, (2 * a + 1) & 3);
         if (words_out) {
           words_out[2 * a] = uh;
@@ -152,25 +152,29 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   return J;
 }
 
-// Tiles between compensated folds of the CTA histogram (ACC 2): the plain
-// FP32 cells then add at most this many bucket sums.
-constexpr int kFoldTiles = 8;
+// Points per thread between compensated folds of the CTA histogram (ACC 2):
+// the plain FP32 cells add the bucket sums of at most this many points per
+// thread before they are folded into the pairs.
+constexpr int kFoldPoints = 8;
 
 // Bucketed tile histogram of one CTA (shared memory).  Shared-memory float
 // atomics are compare-and-swap loops on this GPU while 32-bit integer
 // atomics are native, so a point claims a slot of each of its (axis, bin)
 // buckets with one integer atomicAdd and stores w there (scatter); at the end
 // of a tile one thread per cell sums its bucket into the CTA's cells, w and
-// w^2 (gather).  Full buckets spill into an overflow histogram.  Layout from
-// the base: counters [d N] (int), buckets [cap][d N] (H), overflow [2][d N]
-// (H), cells [2][d N] (H), and for ACC 2 compensated pairs [2][d N].
+// w^2 (gather).  A claim past the capacity stores into a spare row that is
+// never read and sets a bit of a per-point mask; the rare point with a set
+// bit adds those values to an overflow histogram with float atomics, off the
+// common path (no branch per axis).  Layout from the base: counters [d N]
+// (int), buckets [cap + 1][d N] (H), overflow [2][d N] (H), cells [2][d N]
+// (H), and for ACC 2 compensated pairs [2][d N].
 template <int ACC>
 struct TileHist {
   using H = typename AccTraits<ACC>::H;
   static constexpr bool COMP = ACC == 2;
   static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
   static __host__ __device__ size_t off_bucket(int dN) { return a16((size_t)dN * sizeof(int)); }
-  static __host__ __device__ size_t off_ovf(int dN, int cap) { return a16(off_bucket(dN) + (size_t)cap * dN * sizeof(H)); }
+  static __host__ __device__ size_t off_ovf(int dN, int cap) { return a16(off_bucket(dN) + (size_t)(cap + 1) * dN * sizeof(H)); }
   static __host__ __device__ size_t off_cta(int dN, int cap) { return a16(off_ovf(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
   static __host__ __device__ size_t off_comp(int dN, int cap) { return a16(off_cta(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
   static __host__ __device__ size_t bytes(int dN, int cap) {
@@ -182,13 +186,15 @@ struct TileHist {
   H* ovf;
   H* cta;
   fpair* cmp;
-  int N, dN, cap, tile;
+  int N, dN, cap, tile, fold_every;
 
-  __device__ __forceinline__ void bind(unsigned char* base, int dN_, int N_, int cap_) {
+  // ppt: points per thread per tile
+  __device__ __forceinline__ void bind(unsigned char* base, int dN_, int N_, int cap_, int ppt) {
     dN = dN_;
     N = N_;
     cap = cap_;
     tile = 0;
+    fold_every = max(1, kFoldPoints / ppt);
     cnt = reinterpret_cast<int*>(base);
     bucket = reinterpret_cast<H*>(base + off_bucket(dN));
     ovf = reinterpret_cast<H*>(base + off_ovf(dN, cap));
@@ -206,24 +212,34 @@ struct TileHist {
   }
   template <int DM>
   __device__ __forceinline__ void scatter(const int (&kb)[DM], int d, H w) {
+    static_assert(DM <= 32, "one mask bit per axis");
+    uint32_t full = 0;
 #pragma unroll
     for (int a = 0; a < DM; ++a)
       if (a < d) {
         const int cell = a * N + kb[a];
         const int pos = atomicAdd(&cnt[cell], 1);
-        if (pos < cap) {
-          bucket[pos * dN + cell] = w;
-        } else {
-          atomicAdd(&ovf[cell], w);
-          atomicAdd(&ovf[dN + cell], w * w);
-        }
+        bucket[min(pos, cap) * dN + cell] = w;
+        full |= (uint32_t)(pos >= cap) << a;
+      }
+    if (__builtin_expect(full != 0u, 0)) spill<DM>(kb, d, w, full);
+  }
+  template <int DM>
+  __device__ __forceinline__ void spill(const int (&kb)[DM], int d, H w, uint32_t full) {
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d && ((full >> a) & 1u)) {
+        const int cell = a * N + kb[a];
+        atomicAdd(&ovf[cell], w);
+        atomicAdd(&ovf[dN + cell], w * w);
       }
   }
   // End of a tile (all threads of the CTA); ACC 2 folds the FP32 cells into
-  // the compensated pairs every kFoldTiles tiles.
+  // the compensated pairs every kFoldPoints points per thread.
   __device__ __forceinline__ void gather(int tid, int nthr) {
     __syncthreads();
-    const bool fold = COMP && (++tile % kFoldTiles == 0);
+    const bool fold = COMP && (++tile == fold_every);
+    if (fold) tile = 0;
     for (int cell = tid; cell < dN; cell += nthr) {
       const int n = min(cnt[cell], cap);
       H s1 = H(0), s2 = H(0);
@@ -301,7 +317,7 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + L::params(dN));
   TileHist<ACC> hist;
-  hist.bind(smem + L::hist(dN), dN, N, cap);
+  hist.bind(smem + L::hist(dN), dN, N, cap, A.ppt);
 
   // Coalesced, vectorised grid-table load (one 8- or 16-byte cell per bin).
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
@@ -341,6 +357,7 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x;
     const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
     uint64_t s = first + tid;
+    int pend = 0;  // points per thread since the last gather (uniform in the CTA)
     for (uint64_t r = 0; r < rounds; ++r, s += stride) {
       if (s < A.ncall) {
         int kb[DM];
@@ -349,8 +366,12 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
         sw2.add(w * w);
         scatter(kb, w);
       }
-      gather();
+      if (++pend == A.ppt) {
+        gather();
+        pend = 0;
+      }
     }
+    if (pend) gather();
     if constexpr (COMP) {
       tp[0] = sw.p;
       tp[1] = sw2.p;
@@ -374,6 +395,7 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
     const uint32_t cmask = A.ncubes - 1u;
     const uint32_t per_lane = (A.nc + Lw - 1) / Lw;
     uint32_t gi = gfirst + tid / Lw;
+    int pend = 0;  // points per thread since the last gather (uniform in the CTA)
     for (uint32_t r = 0; r < rounds; ++r, gi += gstride) {
       const bool live = gi < A.ncubes;  // uniform within a group
       const uint32_t c = A.cube_mul == 1u ? gi : (gi * A.cube_mul) & cmask;
@@ -404,7 +426,10 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
           p2 += w * w;
           scatter(kb, w);
         }
-        gather();
+        if (++pend == A.ppt) {
+          gather();
+          pend = 0;
+        }
       }
       if constexpr (COMP) {
         fpair c1{p1, 0.f}, c2{p2, 0.f};
@@ -456,6 +481,7 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
         }
       }
     }
+    if (pend) gather();
   }
   __syncthreads();
 

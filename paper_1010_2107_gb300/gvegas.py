@@ -84,6 +84,8 @@ _SIGS = {
     "vegas_set_launch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "vegas_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "vegas_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vegas_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_microbench": (ctypes.c_int, [ctypes.c_int, _DP]),
     "vegas_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
@@ -294,6 +296,16 @@ def vegas_get_launch(ctx: Context):
     t, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().vegas_get_launch(ctx.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(o)), ctx.handle)
     return dict(threads=t.value, ctas=c.value, occupancy=o.value)
+
+
+def vegas_set_tile(ctx: Context, points_per_thread: int = 0):
+    _check(lib().vegas_set_tile(ctx.handle, int(points_per_thread)), ctx.handle)
+
+
+def vegas_get_tile(ctx: Context):
+    p, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib().vegas_get_tile(ctx.handle, ctypes.byref(p), ctypes.byref(c)), ctx.handle)
+    return dict(points_per_thread=p.value, cap=c.value)
 
 
 def vegas_profile_pass(ctx: Context, n_pass: int = 10):
