@@ -240,8 +240,9 @@ vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
 /* Histogram tile of the sampling kernel (no counterpart in the paper, whose
  * host code sums the bins): each thread evaluates `points_per_thread`
  * points (1..8; 0 = automatic) between two gathers of the CTA's
- * (axis, bin) buckets.  Changes only speed and the summation order inside
- * a CTA, never which points are drawn.  get_tile returns the points per
+ * (axis, bin) buckets; kernels that evaluate two points per thread at a
+ * time round it up to even.  Changes only speed and the summation order
+ * inside a CTA, never which points are drawn.  get_tile returns the points per
  * thread and the bucket capacity per (axis, bin) in use.  EINVAL outside
  * the range or when the tile does not fit in shared memory (the previous
  * shape then stays). */
@@ -252,8 +253,10 @@ vegas_status vegas_get_tile(vegas_ctx* ctx, int* points_per_thread, int* cap);
  * kernel): runs n_pass evaluation passes at the current iteration index
  * (no refinement, window untouched) with CUDA events recorded on the
  * context stream around each kernel, and returns the mean milliseconds per
- * launch of ms[0] the sampling kernel, ms[1] the reduction, ms[2] the
- * finalisation.  Synchronises the stream. */
+ * launch of ms[0] the sampling kernel, ms[1] the finishing kernel (the
+ * fixed-order reduction of the per-CTA partials, then refinement and
+ * combination when a pass asks for them), ms[2] the two together.
+ * Synchronises the stream. */
 vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
 
 /* ------------------------------------------------------------------------

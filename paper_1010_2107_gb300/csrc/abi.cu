@@ -50,7 +50,7 @@ struct vegas_ctx {
   // launch geometry
   int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, lanes_req = 0, occ = 0;
   int cap = 16;  // histogram bucket capacity (see sample_kernel.cuh)
-  int ppt = 1, ppt_req = 0;  // points per thread per histogram tile
+  int ppt = 1, ppt_req = 0, ppt_min = 1;  // points per thread per histogram tile
   size_t smem = 0;
   // device buffers
   double* d_edges = nullptr;
@@ -149,7 +149,7 @@ vegas_status configure_launch(vegas_ctx* c) {
   int occ_cap = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c->ke.sample, c->threads, 0);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
-  const gv::TileShape t = gv::choose_tile(c->threads, N, c->ppt_req, occ_cap, occ_of);
+  const gv::TileShape t = gv::choose_tile(c->threads, N, c->ppt_req, c->ppt_min, occ_cap, occ_of);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   if (t.occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %d points per thread",
                                 c->threads, t.ppt);
@@ -261,8 +261,7 @@ vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record) 
   void* args[] = {&A};
   CK(c, cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream));
   gv::FinArgs F = fin_args(c, refine, record);
-  CK(c, gv_launch_reduce(&F, c->stream));
-  CK(c, gv_launch_finalize(&F, c->stream));
+  CK(c, gv_launch_finish(&F, c->stream));
   return VEGAS_OK;
 }
 
@@ -452,8 +451,10 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
     return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
   }
   // the specialised kernel when the shape allows it (see kernels.h)
-  if (c->ke.sample_spec && d == c->ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256)
+  if (c->ke.sample_spec && d == c->ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256) {
     c->ke.sample = c->ke.sample_spec;
+    c->ppt_min = c->ke.spec_ppt_min;
+  }
   auto bail = [&](vegas_status st) {
     g_thread_err = c->err;
     vegas_destroy(c);
@@ -839,8 +840,8 @@ vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
   const uint32_t it = c->h_st->it;
   int zero = 0;
   CK(c, cudaMemcpyAsync(&c->d_st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; ++i) CK(c, cudaEventCreate(&ev[i]));
+  cudaEvent_t ev[3];
+  for (int i = 0; i < 3; ++i) CK(c, cudaEventCreate(&ev[i]));
   double acc[3] = {0, 0, 0};
   cudaError_t e = cudaSuccess;
   for (int p = 0; p < n_pass && e == cudaSuccess; ++p) {
@@ -850,18 +851,18 @@ vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
     e = cudaEventRecord(ev[0], c->stream);
     if (!e) e = cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream);
     if (!e) e = cudaEventRecord(ev[1], c->stream);
-    if (!e) e = gv_launch_reduce(&F, c->stream);
+    if (!e) e = gv_launch_finish(&F, c->stream);
     if (!e) e = cudaEventRecord(ev[2], c->stream);
-    if (!e) e = gv_launch_finalize(&F, c->stream);
-    if (!e) e = cudaEventRecord(ev[3], c->stream);
-    if (!e) e = cudaEventSynchronize(ev[3]);
-    for (int k = 0; k < 3 && !e; ++k) {
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
-      acc[k] += t;
-    }
+    if (!e) e = cudaEventSynchronize(ev[2]);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    if (!e) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (!e) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    if (!e) e = cudaEventElapsedTime(&t2, ev[0], ev[2]);
+    acc[0] += t0;
+    acc[1] += t1;
+    acc[2] += t2;
   }
-  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 3; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "profile: %s", cudaGetErrorString(e));
   for (int k = 0; k < 3; ++k) ms[k] = acc[k] / n_pass;
   return VEGAS_OK;
@@ -963,8 +964,11 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   gv::KernelEntry ke{};
   if (!lookup_kernel(fn->kind, cfg->precision, ybits, d, &ke))
     return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
-  if (ke.sample_spec && d == ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256)
+  int ppt_min = 1;
+  if (ke.sample_spec && d == ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256) {
     ke.sample = ke.sample_spec;
+    ppt_min = ke.spec_ppt_min;
+  }
 
   // Per-device set-up on the first call for the current device: the device
   // address of the scratch array (its host-side name is only a stand-in).
@@ -1003,7 +1007,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   };
   int occ_cap = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, ke.sample, threads, 0);
-  const gv::TileShape t = e == cudaSuccess ? gv::choose_tile(threads, N, 0, occ_cap, occ_of) : gv::TileShape{1, 4, 0};
+  const gv::TileShape t = e == cudaSuccess ? gv::choose_tile(threads, N, 0, ppt_min, occ_cap, occ_of) : gv::TileShape{1, 4, 0};
   if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   if (t.occ < 1) return thread_fail(VEGAS_EINVAL, "sampling kernel does not fit in shared memory");
   const int ppt = t.ppt, cap = t.cap, occ = t.occ;
@@ -1106,8 +1110,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   F.tab64 = reinterpret_cast<double2*>(scratch + off_t64);
   F.tab32 = reinterpret_cast<float2*>(scratch + off_t32);
   F.st = st;
-  if (e == cudaSuccess) e = gv_launch_reduce(&F, s);
-  if (e == cudaSuccess) e = gv_launch_finalize(&F, s);
+  if (e == cudaSuccess) e = gv_launch_finish(&F, s);
   if (e == cudaSuccess) {
     k_noalloc_result<<<1, 1, 0, s>>>(st, out + 2 * (size_t)dN);
     e = cudaGetLastError();

@@ -133,6 +133,10 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   int cd[DM];
 #pragma unroll
   for (int a = 0; a < DM; ++a) cd[a] = 0;
+  // one layout for every instance (sized for kBatchDM axes); the bucket
+  // slots are cleared once and every gather leaves them cleared
+  hist.bind(smem + L::hist(N), kBatchDM * N, N, B.cap, B.ppt, kBatchDM * N);
+  hist.zero_buckets(tid, blockDim.x, kBatchDM * N);
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(B.head, 1);
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
       for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)dp[i];
       cur = W.inst;
     }
-    hist.bind(smem + L::hist(N), dN, N, B.cap, B.ppt);
+    hist.bind(smem + L::hist(N), dN, N, B.cap, B.ppt, kBatchDM * N);
     hist.zero(tid, blockDim.x);
     __syncthreads();
     A.d = d;
@@ -265,9 +269,10 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
       s2[k] = S2;
     }
     __syncthreads();
-    if (B.refine)
+    const Team t{min((int)blockDim.x, (N + 31) / 32 * 32)};  // one thread per bin, whole warps
+    if (B.refine && (int)threadIdx.x < t.n)
       refine_axis_core(s2, B.edges + I.edge_off + (size_t)a * (N + 1), B.tab64 + I.tab_off + (size_t)a * N,
-                       B.tab32 + I.tab_off + (size_t)a * N, N, I.alpha);
+                       B.tab32 + I.tab_off + (size_t)a * N, N, I.alpha, t);
     return;
   }
   const int i = b - B.naxes;
@@ -480,7 +485,7 @@ vegas_status configure(vegas_batch* b) {
   };
   int occ_cap = 0;
   BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, b->kernel, b->threads, 0));
-  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, occ_cap, occ_of);
+  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, 1, occ_cap, occ_of);
   BK(b, e);
   if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
   b->smem = batch_smem(b->prec, b->N, t.cap);

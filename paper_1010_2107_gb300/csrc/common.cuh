@@ -137,7 +137,7 @@ template <> struct Vec2<float> { using type = float2; };
 struct GState {
   uint32_t it;          // Philox iteration counter: iterations run so far
   int done;             // set when the ACC test stops the current call
-  int live;             // latched per pass by k_reduce: 1 if the pass ran
+  int live;             // latched per pass by the sampling kernel: 1 if it ran
   int nhist;            // iterations in the combination window
   int stopped;
   long long nonfinite;  // non-finite weights in the window
@@ -150,8 +150,12 @@ struct GState {
   double ph1_I, ph1_sigma, ph1_chi2;
   int ph1_iters, ph1_stopped;
   long long ph1_nonfinite, ph1_samples;
+  unsigned arrive[kMaxDim + 1];  // block arrivals per group of k_finish (reset by the last)
   double hist[kMaxHist][2];
 };
+
+// Threads per block of k_finish.
+constexpr int kFinishThreads = 256;
 
 // Device-side control operations captured into the iteration graphs.
 enum { CTL_RESET_WINDOW = 1, CTL_SET_ACC = 2, CTL_SNAPSHOT = 4 };
@@ -179,7 +183,7 @@ struct SampleArgs {
   int nparts;              // number of CTAs == partial rows
   const void* tab;         // [d][N] (e_k, Delta_k) in the kernel precision
   const double* dparams;   // derived integrand constants
-  const GState* st;
+  GState* st;              // the sampling kernel latches st->live
   void* part_bins;         // [2 d N][nparts]: double, or float (hi, lo) pairs (FP32 forms)
   double* part_tot;        // [kTotCols][nparts]
   void* cubes;             // [ncubes]: double (sum w, sum w^2), or float (hi, lo, hi, lo)

@@ -1,45 +1,37 @@
 // finalize.cu -- steps 4-6 of Sec. 2.1 after the sampling pass, all on the
-// GPU in FP64 (the paper ran them on the host, Sec. 2.2):
-//   k_reduce    fixed-order reduction of the per-CTA partial rows into the
+// GPU in FP64 (the paper ran them on the host, Sec. 2.2), in one launch:
+//   k_finish    fixed-order reduction of the per-CTA partial rows into the
 //               per-bin sums S1, S2 and the iteration totals (one warp per
-//               column; lanes stride the rows, then an xor butterfly);
-//   k_finalize  per axis: grid optimisation (Lepage 1978: smoothing,
-//               log-compression with exponent alpha, rebinning to equal
-//               weight); one more block: the iteration estimate, the
-//               inverse-variance combination, chi^2 and the ACC test.
+//               column; lanes stride the rows, then an xor butterfly); the
+//               last block of each axis then runs the grid optimisation
+//               (Lepage 1978: smoothing, log-compression with exponent
+//               alpha, rebinning to equal weight) and the last block of the
+//               totals the iteration estimate, the inverse-variance
+//               combination, chi^2 and the ACC test.
 #include "common.cuh"
 #include "kernels.h"
 #include "refine.cuh"
 
 namespace gv {
 
-__global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
-  GState* st = F.st;
-  const int stop = st->done;  // nobody writes `done` while k_reduce runs
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->live = !stop;
-  if (stop) return;  // the ACC test stopped this call; no sampling pass ran
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int dN = F.d * F.N;
-  const int np = F.nparts;
-  const double* src;
-  double sc;
-  double* dst;
+// Fixed-order sum of one column of per-CTA partials by one warp (lanes
+// stride the rows, eight loads in flight, then an xor butterfly); compensated
+// FP32 pairs or doubles.  Returns the sum on every lane.
+__device__ double column_sum(const FinArgs& F, int col, int lane) {
+  const int dN = F.d * F.N, np = F.nparts;
   if (col < 2 * dN && F.pair32) {
-    // compensated FP32 pairs: fixed-order compensated sum, one conversion
     const float2* p = reinterpret_cast<const float2*>(F.part_bins) + (size_t)col * np;
     fpair acc{0.f, 0.f};
     int r = lane;
-    // eight loads in flight per lane, merged in row order
     for (; r + 7 * 32 < np; r += 8 * 32) {
       float2 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = p[r + 32 * j];
+      for (int j = 0; j < 8; ++j) v[j] = __ldcg(p + r + 32 * j);
 #pragma unroll
       for (int j = 0; j < 8; ++j) comp_merge(acc, fpair{v[j].x, v[j].y});
     }
     for (; r < np; r += 32) {
-      const float2 v = p[r];
+      const float2 v = __ldcg(p + r);
       comp_merge(acc, fpair{v.x, v.y});
     }
 #pragma unroll
@@ -49,41 +41,38 @@ __global__ void __launch_bounds__(256) k_reduce(const FinArgs F) {
       o.lo = __shfl_xor_sync(0xffffffffu, acc.lo, off);
       comp_merge(acc, o);
     }
-    if (lane == 0) F.bins[col] = comp_value(acc) * (col < dN ? F.scale : F.scale * F.scale);
-    return;
+    return comp_value(acc);
   }
-  if (col < 2 * dN) {
-    src = reinterpret_cast<const double*>(F.part_bins) + (size_t)col * np;
-    sc = col < dN ? F.scale : F.scale * F.scale;
-    dst = F.bins + col;
-  } else if (col < 2 * dN + 5) {
-    const int q = col - 2 * dN;
-    src = F.part_tot + (size_t)q * np;
-    sc = (q == TOT_SW || q == TOT_SI) ? F.scale
-         : (q == TOT_NONFINITE ? 1.0 : F.scale * F.scale);
-    dst = F.tot + q;
-  } else {
-    return;
-  }
+  const double* src = col < 2 * dN ? reinterpret_cast<const double*>(F.part_bins) + (size_t)col * np
+                                   : F.part_tot + (size_t)(col - 2 * dN) * np;
   double acc = 0.0;
   int r = lane;
   for (; r + 7 * 32 < np; r += 8 * 32) {
     double v[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = src[r + 32 * j];
+    for (int j = 0; j < 8; ++j) v[j] = __ldcg(src + r + 32 * j);
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc += v[j];
   }
-  for (; r < np; r += 32) acc += src[r];
+  for (; r < np; r += 32) acc += __ldcg(src + r);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) *dst = acc * sc;
+  return acc;
 }
 
+// Refinement of axis a from its S2 column sums, which other blocks of this
+// launch wrote: read past L1 into shared memory first.  One thread per bin
+// (whole warps) takes part; the other warps leave.
 __device__ void refine_axis(const FinArgs& F, int a) {
+  __shared__ double s2[kMaxBins];
   const int N = F.N;
-  refine_axis_core(F.bins + (size_t)F.d * N + (size_t)a * N, F.edges + (size_t)a * (N + 1),
-                   F.tab64 + (size_t)a * N, F.tab32 + (size_t)a * N, N, F.alpha);
+  const Team t{min((int)blockDim.x, (N + 31) / 32 * 32)};
+  if ((int)threadIdx.x >= t.n) return;
+  const double* src = F.bins + (size_t)F.d * N + (size_t)a * N;
+  for (int k = threadIdx.x; k < N; k += t.n) s2[k] = __ldcg(src + k);
+  t.sync();
+  refine_axis_core(s2, F.edges + (size_t)a * (N + 1), F.tab64 + (size_t)a * N, F.tab32 + (size_t)a * N, N,
+                   F.alpha, t);
 }
 
 // Step 6 for the pass, by one full warp (lane 0 writes the state).
@@ -139,12 +128,50 @@ __device__ void record_iteration(const FinArgs& F) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_finalize(const FinArgs F) {
-  // `live` was latched by k_reduce of this pass; the ACC test below writes
-  // only `done`, so every block sees the same decision.
-  if (!F.st->live) return;
-  if ((int)blockIdx.x < F.d) {
-    if (F.refine) refine_axis(F, blockIdx.x);
+// Steps 4-6 after a sampling pass in one launch.  Blocks come in groups:
+// group a < d reduces the 2N columns (S1, S2) of axis a, one warp per
+// column, and the last of its blocks to finish (an arrival counter, after
+// a memory fence) refines axis a; the final group reduces the iteration
+// totals and records the iteration.  No block waits for another: the last
+// arrival does the dependent work.  `live` was latched by the sampling
+// kernel of this pass and the ACC test below writes only `done`.
+__global__ void __launch_bounds__(kFinishThreads) k_finish(const FinArgs F) {
+  GState* st = F.st;
+  if (!st->live) return;
+  const int wpb = kFinishThreads / 32, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int N = F.N, dN = F.d * N;
+  const int bpa = (2 * N + wpb - 1) / wpb;  // blocks per axis
+  const int b = blockIdx.x;
+  const int group = b < F.d * bpa ? b / bpa : F.d;
+  if (group < F.d) {
+    const int a = group, i = (b - a * bpa) * wpb + warp;  // column of the axis, 0 .. 2N
+    if (i < 2 * N) {
+      const int col = i < N ? a * N + i : dN + a * N + (i - N);
+      const double v = column_sum(F, col, lane);
+      if (lane == 0) F.bins[col] = v * (i < N ? F.scale : F.scale * F.scale);
+    }
+  } else if (warp < kTotCols) {
+    const int q = warp;
+    if (q < 5) {
+      const double v = column_sum(F, 2 * dN + q, lane);
+      const double sc = (q == TOT_SW || q == TOT_SI) ? F.scale : (q == TOT_NONFINITE ? 1.0 : F.scale * F.scale);
+      if (lane == 0) F.tot[q] = v * sc;
+    }
+  }
+  // arrival: the group's last block continues
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int n = group < F.d ? bpa : 1;
+    last = atomicAdd(&st->arrive[group], 1u) == (unsigned)(n - 1);
+    if (last) st->arrive[group] = 0;  // ready for the next pass
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (group < F.d) {
+    if (F.refine) refine_axis(F, group);
   } else if (threadIdx.x < 32) {
     record_iteration(F);
   }
@@ -212,7 +239,7 @@ extern "C" {
 // shared memory; the small kernels between them ask for the same split, so
 // that an SM need not change its partition (and drain) at every boundary.
 cudaError_t gv_prepare_aux_kernels(void) {
-  const void* fns[] = {(const void*)gv::k_reduce, (const void*)gv::k_finalize, (const void*)gv::k_colsum,
+  const void* fns[] = {(const void*)gv::k_finish, (const void*)gv::k_colsum,
                        (const void*)gv::k_control, (const void*)gv::k_uniform_grid, (const void*)gv::k_tables};
   for (const void* f : fns) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -222,15 +249,10 @@ cudaError_t gv_prepare_aux_kernels(void) {
   return cudaSuccess;
 }
 
-cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s) {
-  const int cols = 2 * F->d * F->N + 5;
-  const int wpb = 8;
-  gv::k_reduce<<<(cols + wpb - 1) / wpb, 32 * wpb, 0, s>>>(*F);
-  return cudaGetLastError();
-}
-
-cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s) {
-  gv::k_finalize<<<F->d + 1, 64, 0, s>>>(*F);
+cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s) {
+  const int wpb = gv::kFinishThreads / 32;
+  const int blocks = F->d * ((2 * F->N + wpb - 1) / wpb) + 1;
+  gv::k_finish<<<blocks, gv::kFinishThreads, 0, s>>>(*F);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,8 @@ struct KernelEntry {
   size_t (*smem)(int d, int N, int cap);  // dynamic shared memory of `sample`
                                           // with bucket capacity cap
   int dm;                             // compile-time dimension bound
+  int spec_ppt_min;                   // `sample_spec` evaluates this many points per
+                                      // thread at a time: tiles are multiples of it
   const void* grad;                   // k_grad<T, DM, F, YB> or null
   int grad_nt;                        // its gradient columns (F<T, DM>::NT)
   size_t (*grad_smem)(int d, int N);
@@ -62,15 +64,18 @@ struct TileShape {
 // shared memory).  Larger tiles amortise the gather and its barriers, so
 // the largest ppt in {4, 2, 1} that keeps at least 16 warps per SM (or the
 // most the kernel can have) wins; ppt_req > 0 forces the tile and then halves
-// the capacity until it fits.  occ_of(cap, ppt) returns the CTAs per SM (0:
-// does not fit).
+// the capacity until it fits.  A kernel that evaluates ppt_min points per
+// thread at a time (1 or 2) gets tiles that are multiples of it.
+// occ_of(cap, ppt) returns the CTAs per SM (0: does not fit).
 template <class OccOf>
-inline TileShape choose_tile(int threads, int N, int ppt_req, int occ_cap, OccOf occ_of) {
+inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int occ_cap, OccOf occ_of) {
   auto ceil4 = [](double v) { return ((int)v + 1 + 3) & ~3; };
   TileShape best{0, 0, 0};
   const int wanted = occ_cap * threads / 32 < 16 ? occ_cap * threads / 32 : 16;
   const int cands[3] = {4, 2, 1};
+  if (ppt_req > 0) ppt_req = (ppt_req + ppt_min - 1) / ppt_min * ppt_min;
   for (int i = 0; i < 3; ++i) {
+    if (ppt_req <= 0 && cands[i] < ppt_min) continue;
     const int ppt = ppt_req > 0 ? ppt_req : cands[i];
     const double m = (double)threads * ppt / N;
     int hi = ceil4(m + 4.0 * __builtin_sqrt(m) + 2.0), lo = ceil4(m + 2.0 * __builtin_sqrt(m) + 1.0);
@@ -84,7 +89,8 @@ inline TileShape choose_tile(int threads, int N, int ppt_req, int occ_cap, OccOf
     }
     if (ppt_req > 0) {  // forced tile: shrink the capacity until it fits
       for (int cap = lo; t.occ < 1 && cap > 4;) {
-        cap = cap / 2 < 4 ? 4 : cap / 2;
+        cap = (cap / 2) & ~3;  // capacities stay multiples of 4 (vector gather)
+        cap = cap < 4 ? 4 : cap;
         const int o = occ_of(cap, ppt);
         if (o > 0) t = TileShape{ppt, cap, o};
       }
@@ -96,10 +102,10 @@ inline TileShape choose_tile(int threads, int N, int ppt_req, int occ_cap, OccOf
   if (best.occ > 0) return best;
   // nothing fits at the smallest tile's capacities: halve below them
   for (int cap = 8; cap >= 4; cap /= 2) {
-    const int o = occ_of(cap, 1);
-    if (o > 0) return TileShape{1, cap, o};
+    const int o = occ_of(cap, ppt_min);
+    if (o > 0) return TileShape{ppt_min, cap, o};
   }
-  return TileShape{1, 4, 0};
+  return TileShape{ppt_min, 4, 0};
 }
 
 // Lanes per hypercube (stratified sampling): the smallest power of two L
@@ -129,8 +135,7 @@ struct DumpArgs {
 
 extern "C" {
 cudaError_t gv_prepare_aux_kernels(void);
-cudaError_t gv_launch_reduce(const gv::FinArgs* F, cudaStream_t s);
-cudaError_t gv_launch_finalize(const gv::FinArgs* F, cudaStream_t s);
+cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);
 cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
 cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s);

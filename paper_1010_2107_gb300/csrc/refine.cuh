@@ -14,12 +14,21 @@ __device__ __forceinline__ void two_sum_d(double a, double b, double& s, double&
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Compensated all-reduce over the block (every thread gets the sum).  A
+// The first n threads of a block (n a multiple of 32) working as one team
+// with a barrier of its own (named barrier 1), so that a step needing few
+// threads leaves the other warps idle: scalar FP64 is slow on this GPU and
+// even idle lanes of a warp that issues an FP64 instruction cost its pipe.
+struct Team {
+  int n;
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+};
+
+// Compensated all-reduce over the team (every thread gets the sum).  A
 // thread's values are summed in a fixed tree (xor butterfly within a warp,
 // then the warps in order), each step with TwoSum, so the result is
 // deterministic and its error is that of a twice-as-precise sum.  `buf`:
-// shared scratch of 2 x (warps) doubles; all threads must call.
-__device__ inline double block_sum(double v, double* buf) {
+// shared scratch of 2 x (warps) doubles; all team threads must call.
+__device__ inline double block_sum(double v, double* buf, Team t) {
   double s = v, c = 0.0;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -29,13 +38,13 @@ __device__ inline double block_sum(double v, double* buf) {
     s = t;
     c = c + oc + e;
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();  // buf may still be read from an earlier call
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = t.n >> 5;
+  t.sync();  // buf may still be read from an earlier call
   if (lane == 0) {
     buf[2 * warp] = s;
     buf[2 * warp + 1] = c;
   }
-  __syncthreads();
+  t.sync();
   double S = buf[0], C = buf[1];
   for (int w = 1; w < nw; ++w) {
     double t, e;
@@ -46,21 +55,21 @@ __device__ inline double block_sum(double v, double* buf) {
   return S + C;
 }
 
-// Inclusive prefix sums of x[0..n) into out[0..n) by the block (Hillis-Steele
-// doubling over shared memory; n <= 2 blockDim.x is not required).
-__device__ inline void block_prefix(const double* x, double* out, double* tmp, int n) {
+// Inclusive prefix sums of x[0..n) into out[0..n) by the team (Hillis-Steele
+// doubling over shared memory).
+__device__ inline void block_prefix(const double* x, double* out, double* tmp, int n, Team t) {
   const int tid = threadIdx.x;
-  for (int k = tid; k < n; k += blockDim.x) out[k] = x[k];
-  __syncthreads();
+  for (int k = tid; k < n; k += t.n) out[k] = x[k];
+  t.sync();
   for (int off = 1; off < n; off <<= 1) {
-    for (int k = tid; k < n; k += blockDim.x) tmp[k] = k >= off ? out[k] + out[k - off] : out[k];
-    __syncthreads();
-    for (int k = tid; k < n; k += blockDim.x) out[k] = tmp[k];
-    __syncthreads();
+    for (int k = tid; k < n; k += t.n) tmp[k] = k >= off ? out[k] + out[k - off] : out[k];
+    t.sync();
+    for (int k = tid; k < n; k += t.n) out[k] = tmp[k];
+    t.sync();
   }
 }
 
-// One axis, one thread block: smooth the per-bin sums of w^2 over
+// One axis, one team of threads: smooth the per-bin sums of w^2 over
 // neighbours, compress them with r_k = ((1 - d_k/D) / ln(D/d_k))^alpha, and
 // move the edges so that every new bin holds an equal share of sum r, with r
 // spread uniformly inside each old bin.  dd: S2 of the axis (N values);
@@ -74,13 +83,13 @@ __device__ inline void block_prefix(const double* x, double* out, double* tmp, i
 // its loop-carried dependence; FP64 scalar arithmetic is slow on this GPU,
 // so the serial chains are kept short.
 __device__ inline void refine_axis_core(const double* dd, double* ea, double2* t64, float2* t32, int N,
-                                        double alpha) {
+                                        double alpha, Team t) {
   __shared__ double dsm[kMaxBins], r[kMaxBins], e[kMaxBins + 1], enew[kMaxBins + 1], C[kMaxBins + 1],
       tmp[kMaxBins], buf[64];
   const int tid = threadIdx.x;
-  for (int k = tid; k <= N; k += blockDim.x) e[k] = ea[k];
+  for (int k = tid; k <= N; k += t.n) e[k] = ea[k];
   double part = 0.0;
-  for (int k = tid; k < N; k += blockDim.x) {
+  for (int k = tid; k < N; k += t.n) {
     double v;
     if (N == 2)
       v = (dd[0] + dd[1]) / 2.0;
@@ -93,25 +102,25 @@ __device__ inline void refine_axis_core(const double* dd, double* ea, double2* t
     dsm[k] = v;
     part += v;
   }
-  const double D = block_sum(part, buf);
-  if (!(D > 0.0) || !isfinite(D)) return;  // uniform across the block
+  const double D = block_sum(part, buf, t);
+  if (!(D > 0.0) || !isfinite(D)) return;  // uniform across the team
   part = 0.0;
-  for (int k = tid; k < N; k += blockDim.x) {
+  for (int k = tid; k < N; k += t.n) {
     const double x = dsm[k];
     const double rk = x <= 0.0 ? 0.0 : (x >= D ? 1.0 : pow((1.0 - x / D) / log(D / x), alpha));
     r[k] = rk;
     part += rk;
   }
-  const double R = block_sum(part, buf);
+  const double R = block_sum(part, buf, t);
   // C[k + 1] = r_0 + ... + r_k, C[0] = 0
-  block_prefix(r, C + 1, tmp, N);
+  block_prefix(r, C + 1, tmp, N, t);
   if (tid == 0) {
     C[0] = 0.0;
     enew[0] = 0.0;
     enew[N] = 1.0;
   }
-  __syncthreads();
-  for (int j = 1 + tid; j < N; j += blockDim.x) {
+  t.sync();
+  for (int j = 1 + tid; j < N; j += t.n) {
     const double tau = (double)j * R / (double)N;
     // first k in [0, N-1) with C[k + 1] >= tau, else N - 1 (C is nondecreasing)
     int lo = 0, hi = N - 1;
@@ -125,9 +134,9 @@ __device__ inline void refine_axis_core(const double* dd, double* ea, double2* t
     const int k = lo;
     enew[j] = e[k] + (tau - C[k]) / r[k] * (e[k + 1] - e[k]);
   }
-  __syncthreads();
-  for (int k = tid; k <= N; k += blockDim.x) ea[k] = enew[k];
-  for (int k = tid; k < N; k += blockDim.x) {
+  t.sync();
+  for (int k = tid; k <= N; k += t.n) ea[k] = enew[k];
+  for (int k = tid; k < N; k += t.n) {
     const double lo = enew[k], w = enew[k + 1] - enew[k];
     t64[k] = make_double2(lo, w);
     t32[k] = make_float2((float)lo, (float)w);

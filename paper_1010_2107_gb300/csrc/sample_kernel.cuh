@@ -121,6 +121,8 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   const T Nf = T(N);
   T J = T(1);
   uint4 w4 = make_uint4(0, 0, 0, 0);
+  constexpr bool FAST = SPEC && YB == 24 && std::is_same<T, float>::value;
+  const int sh = 24 + A.g_log2;  // SPEC: y g N 2^24 < 2^32, bin k = t >> sh
 #pragma unroll
   for (int a = 0; a < DM; ++a) {
     if (a < d) {
@@ -129,6 +131,19 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
         if ((a & 3) == 0) w4 = philox4x32_10(make_uint4(s, (uint32_t)(a >> 2), it, A.instance), A.ks);
         const uint32_t u = pick(w4, a & 3);
         if (words_out) words_out[a] = u;
+        if constexpr (FAST) {
+          // t = ((c << 24) | (u >> 8)) N, then k = t >> sh and the top 23
+          // bits of t mod 2^sh as the fraction: the same bits as bin_frac
+          // and frac23, with funnel shifts doing the packing
+          const uint32_t t = __funnelshift_r(u, (uint32_t)cd[a], 8) * (uint32_t)N;
+          const int k = (int)(t >> sh);
+          const float fr = __uint_as_float(__funnelshift_r(t << (32 - sh), 0x7Fu, 9)) - 1.0f;
+          const typename Vec2<T>::type e = tab[a * N + k];
+          x[a] = vfma(fr, e.y, e.x);
+          J *= Nf * e.y;
+          kb[a] = k;
+          continue;
+        }
         m = u >> 8;
       } else {
         if (((2 * a) & 3) == 0)
@@ -152,6 +167,11 @@ __device__ __forceinline__ T make_point(const SampleArgs& A, uint32_t it, uint32
   return J;
 }
 
+// Sampling kernels that keep two points per thread in flight: FP32,
+// specialised shape, at most 8 dimensions.
+template <typename T, int DM, bool SPEC>
+constexpr bool kPairPoints = SPEC && std::is_same<T, float>::value && DM <= 8;
+
 // Points per thread between compensated folds of the CTA histogram (ACC 2):
 // the plain FP32 cells add the bucket sums of at most this many points per
 // thread before they are folded into the pairs.
@@ -162,77 +182,90 @@ constexpr int kFoldPoints = 8;
 // atomics are native, so a point claims a slot of each of its (axis, bin)
 // buckets with one integer atomicAdd and stores w there (scatter); at the end
 // of a tile one thread per cell sums its bucket into the CTA's cells, w and
-// w^2 (gather).  A claim past the capacity stores into a spare row that is
-// never read and sets a bit of a per-point mask; the rare point with a set
-// bit adds those values to an overflow histogram with float atomics, off the
-// common path (no branch per axis).  Layout from the base: counters [d N]
-// (int), buckets [cap + 1][d N] (H), overflow [2][d N] (H), cells [2][d N]
-// (H), and for ACC 2 compensated pairs [2][d N].
+// w^2 (gather).  Buckets are cell-major rows of S = cap + V slots (V values
+// per 16 bytes), so the gather reads and clears four slots per vector load
+// and store; slots past a bucket's fill are zero (cleared after every read),
+// so the reads need no masking.  A claim past the capacity stores into the
+// spare slot `cap` (never read) and the point, which remembers the largest
+// claim it made, then adds those values to the cells with float atomics,
+// off the common path.  Layout from the base: counters [d N] (int), buckets
+// [d N][S] (H), cells [2][d N] (H), and for ACC 2 compensated pairs [2][d N].
 template <int ACC>
 struct TileHist {
   using H = typename AccTraits<ACC>::H;
   static constexpr bool COMP = ACC == 2;
+  static constexpr int V = 16 / (int)sizeof(H);  // slots per 16-byte vector
+  using HV = typename std::conditional<sizeof(H) == 4, float4, double2>::type;
+  static __host__ __device__ int stride(int cap) { return cap + V; }
   static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
   static __host__ __device__ size_t off_bucket(int dN) { return a16((size_t)dN * sizeof(int)); }
-  static __host__ __device__ size_t off_ovf(int dN, int cap) { return a16(off_bucket(dN) + (size_t)(cap + 1) * dN * sizeof(H)); }
-  static __host__ __device__ size_t off_cta(int dN, int cap) { return a16(off_ovf(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
+  static __host__ __device__ size_t off_cta(int dN, int cap) {
+    return a16(off_bucket(dN) + (size_t)stride(cap) * dN * sizeof(H));
+  }
   static __host__ __device__ size_t off_comp(int dN, int cap) { return a16(off_cta(dN, cap) + 2 * (size_t)dN * sizeof(H)); }
   static __host__ __device__ size_t bytes(int dN, int cap) {
     return off_comp(dN, cap) + (COMP ? 2 * (size_t)dN * sizeof(fpair) : 0);
   }
 
   int* cnt;
-  H* bucket;  // [cap][d N]: slot-major, so a gather over consecutive cells is conflict-free
-  H* ovf;
+  H* bucket;  // [d N][S]
   H* cta;
   fpair* cmp;
-  int N, dN, cap, tile, fold_every;
+  int N, dN, cap, S, tile, fold_every;
 
-  // ppt: points per thread per tile
-  __device__ __forceinline__ void bind(unsigned char* base, int dN_, int N_, int cap_, int ppt) {
+  // dN cells in use of a layout sized for `cells` >= dN; cap: a multiple of
+  // 4; ppt: points per thread per tile
+  __device__ __forceinline__ void bind(unsigned char* base, int dN_, int N_, int cap_, int ppt, int cells) {
     dN = dN_;
     N = N_;
     cap = cap_;
+    S = stride(cap_);
     tile = 0;
     fold_every = max(1, kFoldPoints / ppt);
     cnt = reinterpret_cast<int*>(base);
-    bucket = reinterpret_cast<H*>(base + off_bucket(dN));
-    ovf = reinterpret_cast<H*>(base + off_ovf(dN, cap));
-    cta = reinterpret_cast<H*>(base + off_cta(dN, cap));
-    cmp = reinterpret_cast<fpair*>(base + off_comp(dN, cap));
+    bucket = reinterpret_cast<H*>(base + off_bucket(cells));
+    cta = reinterpret_cast<H*>(base + off_cta(cells, cap));
+    cmp = reinterpret_cast<fpair*>(base + off_comp(cells, cap));
   }
-  // Clear everything (the caller synchronises before the first scatter).
+  // Clear the bucket slots of `cells` cells: once per launch, since every
+  // gather leaves the slots it read cleared (the caller synchronises).
+  __device__ __forceinline__ void zero_buckets(int tid, int nthr, int cells) {
+    HV* b = reinterpret_cast<HV*>(bucket);
+    const HV z{};
+    for (int i = tid; i < cells * S / V; i += nthr) b[i] = z;
+  }
+  // Clear counters and cells (the caller synchronises before the first
+  // scatter).
   __device__ __forceinline__ void zero(int tid, int nthr) {
     for (int i = tid; i < dN; i += nthr) cnt[i] = 0;
     for (int i = tid; i < 2 * dN; i += nthr) {
-      ovf[i] = H(0);
       cta[i] = H(0);
       if (COMP) cmp[i] = fpair{0.f, 0.f};
     }
   }
   template <int DM>
   __device__ __forceinline__ void scatter(const int (&kb)[DM], int d, H w) {
-    static_assert(DM <= 32, "one mask bit per axis");
-    uint32_t full = 0;
+    int pos[DM];
+    int top = 0;
 #pragma unroll
     for (int a = 0; a < DM; ++a)
       if (a < d) {
         const int cell = a * N + kb[a];
-        const int pos = atomicAdd(&cnt[cell], 1);
-        bucket[min(pos, cap) * dN + cell] = w;
-        full |= (uint32_t)(pos >= cap) << a;
+        pos[a] = atomicAdd(&cnt[cell], 1);
+        bucket[cell * S + min(pos[a], cap)] = w;
+        top = max(top, pos[a]);
       }
-    if (__builtin_expect(full != 0u, 0)) spill<DM>(kb, d, w, full);
-  }
-  template <int DM>
-  __device__ __forceinline__ void spill(const int (&kb)[DM], int d, H w, uint32_t full) {
+    if (__builtin_expect(top >= cap, 0)) {
+      // spare-slot claims: add to the cells directly (nothing reads them
+      // before the gather's barrier)
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d && ((full >> a) & 1u)) {
-        const int cell = a * N + kb[a];
-        atomicAdd(&ovf[cell], w);
-        atomicAdd(&ovf[dN + cell], w * w);
-      }
+      for (int a = 0; a < DM; ++a)
+        if (a < d && pos[a] >= cap) {
+          const int cell = a * N + kb[a];
+          atomicAdd(&cta[cell], w);
+          atomicAdd(&cta[dN + cell], w * w);
+        }
+    }
   }
   // End of a tile (all threads of the CTA); ACC 2 folds the FP32 cells into
   // the compensated pairs every kFoldPoints points per thread.
@@ -240,20 +273,38 @@ struct TileHist {
     __syncthreads();
     const bool fold = COMP && (++tile == fold_every);
     if (fold) tile = 0;
+    const HV z{};
     for (int cell = tid; cell < dN; cell += nthr) {
-      const int n = min(cnt[cell], cap);
+      const int nq = (min(cnt[cell], cap) + V - 1) / V;  // vectors holding the fill
+      HV* row = reinterpret_cast<HV*>(bucket + (size_t)cell * S);
       H s1 = H(0), s2 = H(0);
-      int j = 0;
-      for (; j + 4 <= n; j += 4) {
-        const H v0 = bucket[j * dN + cell], v1 = bucket[(j + 1) * dN + cell];
-        const H v2 = bucket[(j + 2) * dN + cell], v3 = bucket[(j + 3) * dN + cell];
-        s1 += (v0 + v1) + (v2 + v3);
-        s2 += (v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3);
+      // FP32: two-lane sums with the paired FP32 instructions (one add and
+      // one fused square-add per two slots)
+      float2 a1 = make_float2(0.f, 0.f), a2 = make_float2(0.f, 0.f);
+      // four vectors per step: the loads issue together, then the clears
+      for (int q = 0; q < nq; q += 4) {
+        HV v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = q + u < nq ? row[q + u] : z;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (q + u < nq) row[q + u] = z;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if constexpr (V == 4) {
+            const float2 lo = make_float2(v[u].x, v[u].y), hi = make_float2(v[u].z, v[u].w);
+            a1 = __fadd2_rn(a1, __fadd2_rn(lo, hi));
+            a2 = __ffma2_rn(lo, lo, a2);
+            a2 = __ffma2_rn(hi, hi, a2);
+          } else {
+            s1 += v[u].x + v[u].y;
+            s2 += v[u].x * v[u].x + v[u].y * v[u].y;
+          }
+        }
       }
-      for (; j < n; ++j) {
-        const H v = bucket[j * dN + cell];
-        s1 += v;
-        s2 += v * v;
+      if constexpr (V == 4) {
+        s1 = a1.x + a1.y;
+        s2 = a2.x + a2.y;
       }
       H c1 = cta[cell] + s1, c2 = cta[dN + cell] + s2;
       if (fold) {
@@ -272,10 +323,9 @@ struct TileHist {
   __device__ __forceinline__ fpair pair(int i) const {
     fpair p = cmp[i];
     comp_add(p, (float)cta[i]);
-    comp_add(p, (float)ovf[i]);
     return p;
   }
-  __device__ __forceinline__ double value(int i) const { return (double)cta[i] + (double)ovf[i]; }
+  __device__ __forceinline__ double value(int i) const { return (double)cta[i]; }
 };
 
 // Shared memory layout of k_sample (byte offsets): grid table, integrand
@@ -306,7 +356,11 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   using T2 = typename Vec2<T>::type;
   using L = SmemLayout<T, ACC>;
   constexpr bool COMP = ACC == 2;  // FP32 throughout, no FP64 in the loop
-  if (A.st->done) return;  // the ACC test stopped this call (device-side)
+  // the ACC test stopped this call (device-side): no pass, and k_finish
+  // then skips it too (it reads `live`, nothing else here writes it)
+  const int stop = A.st->done;
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.st->live = !stop;
+  if (stop) return;
   const uint32_t it = A.it_override >= 0 ? (uint32_t)A.it_override : A.st->it;
   // SPEC: d equals the compile-time bound DM, 24-bit words and power-of-two
   // hypercube divisions with g N <= 256: every per-axis guard folds away.
@@ -317,12 +371,13 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + L::params(dN));
   TileHist<ACC> hist;
-  hist.bind(smem + L::hist(dN), dN, N, cap, A.ppt);
+  hist.bind(smem + L::hist(dN), dN, N, cap, A.ppt, dN);
 
   // Coalesced, vectorised grid-table load (one 8- or 16-byte cell per bin).
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
+  hist.zero_buckets(tid, blockDim.x, dN);
   hist.zero(tid, blockDim.x);
   __syncthreads();
 
@@ -335,17 +390,22 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
   auto gather = [&]() { hist.gather(tid, blockDim.x); };
   // w = f J in the kernel precision, widened to the histogram type H
   // (squares are then formed in H: FP64 unless ACC == 2).
-  auto eval_point = [&](uint32_t s, int (&kb)[DM]) -> H {
+  auto eval_point = [&](uint32_t s, int (&kb)[DM], bool valid = true) -> H {
     T x[DM];
     const T J = make_point<T, DM, YB, SPEC>(A, it, s, cd, tab, x, kb, nullptr);
     const T f = F<T, DM>::eval(x, d, P);
     T w = f * J;
     if (!vfinite(w)) {
-      ++nonfinite;
+      nonfinite += valid;
       w = T(0);
     }
     return (H)w;
   };
+  // Two points per thread in flight (specialised FP32 kernels of low
+  // dimension, whose registers allow it): their independent instruction
+  // streams interleave, and the tile then holds an even number of points
+  // per thread.  Sums take the two in order, as one point at a time would.
+  constexpr bool PAIR = kPairPoints<T, DM, SPEC>;
 
   // Totals: sum w, sum w^2, sum of cube means, sum of cube-mean variances;
   // FP64 (ACC 0/1) or compensated FP32 pairs (ACC 2).
@@ -358,17 +418,40 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
     const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
     uint64_t s = first + tid;
     int pend = 0;  // points per thread since the last gather (uniform in the CTA)
-    for (uint64_t r = 0; r < rounds; ++r, s += stride) {
-      if (s < A.ncall) {
-        int kb[DM];
-        const H w = eval_point((uint32_t)s, kb);
-        sw.add(w);
-        sw2.add(w * w);
-        scatter(kb, w);
+    if constexpr (PAIR) {
+      for (uint64_t r = 0; r < rounds; r += 2, s += 2 * stride) {
+        const bool v0 = s < A.ncall, v1 = s + stride < A.ncall;
+        int kb0[DM], kb1[DM];
+        const H w0 = eval_point((uint32_t)s, kb0, v0);
+        const H w1 = eval_point((uint32_t)(s + stride), kb1, v1);
+        if (v0) {
+          sw.add(w0);
+          sw2.add(w0 * w0);
+          scatter(kb0, w0);
+        }
+        if (v1) {
+          sw.add(w1);
+          sw2.add(w1 * w1);
+          scatter(kb1, w1);
+        }
+        if ((pend += 2) >= A.ppt) {
+          gather();
+          pend = 0;
+        }
       }
-      if (++pend == A.ppt) {
-        gather();
-        pend = 0;
+    } else {
+      for (uint64_t r = 0; r < rounds; ++r, s += stride) {
+        if (s < A.ncall) {
+          int kb[DM];
+          const H w = eval_point((uint32_t)s, kb);
+          sw.add(w);
+          sw2.add(w * w);
+          scatter(kb, w);
+        }
+        if (++pend == A.ppt) {
+          gather();
+          pend = 0;
+        }
       }
     }
     if (pend) gather();
@@ -417,18 +500,42 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
       // a lane's chain of points in one cube is short: plain sums in H,
       // compensated merges across the group
       H p1 = H(0), p2 = H(0);
-      for (uint32_t i = 0; i < per_lane; ++i) {
-        const uint32_t j = gl + i * Lw;
-        if (live && j < A.nc) {
-          int kb[DM];
-          const H w = eval_point(s0 + j, kb);
-          p1 += w;
-          p2 += w * w;
-          scatter(kb, w);
+      if constexpr (PAIR) {
+        for (uint32_t i = 0; i < per_lane; i += 2) {
+          const uint32_t j0 = gl + i * Lw, j1 = j0 + Lw;
+          const bool v0 = live && j0 < A.nc, v1 = live && j1 < A.nc;
+          int kb0[DM], kb1[DM];
+          const H w0 = eval_point(s0 + j0, kb0, v0);
+          const H w1 = eval_point(s0 + j1, kb1, v1);
+          if (v0) {
+            p1 += w0;
+            p2 += w0 * w0;
+            scatter(kb0, w0);
+          }
+          if (v1) {
+            p1 += w1;
+            p2 += w1 * w1;
+            scatter(kb1, w1);
+          }
+          if ((pend += 2) >= A.ppt) {
+            gather();
+            pend = 0;
+          }
         }
-        if (++pend == A.ppt) {
-          gather();
-          pend = 0;
+      } else {
+        for (uint32_t i = 0; i < per_lane; ++i) {
+          const uint32_t j = gl + i * Lw;
+          if (live && j < A.nc) {
+            int kb[DM];
+            const H w = eval_point(s0 + j, kb);
+            p1 += w;
+            p2 += w * w;
+            scatter(kb, w);
+          }
+          if (++pend == A.ppt) {
+            gather();
+            pend = 0;
+          }
         }
       }
       if constexpr (COMP) {
@@ -497,8 +604,8 @@ __global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
     }
   }
 
-  __shared__ double wsum[8][5];
-  __shared__ fpair wpair[8][4];
+  __shared__ double wsum[32][5];
+  __shared__ fpair wpair[32][4];
   if constexpr (COMP) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -710,6 +817,7 @@ inline KernelEntry make_entry() {
   e.dump = (const void*)&k_dump<T, DM, F, YB>;
   e.smem = &sample_smem_bytes<T, ACC>;
   e.dm = DM;
+  e.spec_ppt_min = kPairPoints<T, DM, true> ? 2 : 1;
   return e;
 }
 

@@ -309,10 +309,11 @@ def vegas_get_tile(ctx: Context):
 
 
 def vegas_profile_pass(ctx: Context, n_pass: int = 10):
-    """Mean milliseconds per launch of (sampling, reduction, finalisation)."""
+    """Mean milliseconds per pass of the sampling kernel, the finishing kernel
+    (reduction of the partials) and the two together."""
     ms = np.zeros(3)
     _check(lib().vegas_profile_pass(ctx.handle, int(n_pass), _dp(ms)), ctx.handle)
-    return dict(sample=ms[0], reduce=ms[1], finalize=ms[2])
+    return dict(sample=ms[0], finish=ms[1], passes=ms[2])
 
 
 def vegas_eval_noalloc(kind: int, ndim: int, params, edges_ptr: int, it: int, out_ptr: int, *,

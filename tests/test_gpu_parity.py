@@ -176,9 +176,9 @@ def test_acc_stops_early_on_device(gv):
 @pytest.mark.parametrize("N", [2, 31, 33, 64, 65, 100, 256])
 @pytest.mark.parametrize("precision", [0, 2])
 def test_bin_counts_across_histogram_paths(gv, orc, N, precision):
-    """nbins <= 64 uses warp bin ownership, larger counts the atomic path; both
-    must give the oracle's per-bin sums (ragged NCALL, two iterations with a
-    refined grid in between)."""
+    """Bin counts from 2 to 256 change the bucket capacity and tile shape of
+    the CTA histogram; every one must give the oracle's per-bin sums (ragged
+    NCALL, two iterations with a refined grid in between)."""
     d, ncall = 3, 3 * 4096 + 17
     params = wl.genz_gaussian_params(d, a=6.0, u=0.4)
     ctx, cfg, fn = _pair(gv, orc, wl.GENZ_GAUSSIAN, d, params, N=N, ncall=ncall, precision=precision,
@@ -226,3 +226,43 @@ def test_dimension_extremes(gv, orc, d, precision):
     tol = 1e-12 if precision == 0 else 1e-5
     assert I == pytest.approx(o["I"], rel=tol)
     np.testing.assert_allclose(bins[0], o["S1"], rtol=tol, atol=tol * np.abs(o["S1"]).max())
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("ppt", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("nstrat", [0, 4])
+def test_histogram_tile_shapes(gv, orc, precision, ppt, nstrat):
+    """Every histogram tile (points per thread between gathers) gives the
+    oracle's sums: the tile changes only the summation order.  The FP32
+    kernel of d = 8 evaluates two points at a time and rounds odd tiles up."""
+    d, ncall = 8, 4 ** 8 * 3 + (0 if nstrat else 101)
+    params = wl.double_gaussian_params()
+    ctx, cfg, fn = _pair(gv, orc, wl.DOUBLE_GAUSSIAN, d, params, ncall=ncall, nstrat=nstrat,
+                         precision=precision, ybits=24)
+    with ctx:
+        gv.vegas_set_tile(ctx, ppt)
+        t = gv.vegas_get_tile(ctx)
+        I, var = gv.vegas_eval(ctx, 3)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    if precision == 2:
+        assert t["points_per_thread"] == ppt + (ppt % 2)
+    else:
+        assert t["points_per_thread"] == ppt
+    assert t["cap"] >= 4
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 3)
+    p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 3, np.arange(ncall))
+    absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    tol = 1e-12 if precision == 0 else 1e-5
+    assert _cond_close(bins[0], o["S1"], absw.sum(), tol)
+    assert _cond_close(bins[1], o["S2"], (absw ** 2).sum(), tol)
+    assert abs(I - o["I"]) <= tol * absw.mean() + 0.1 * math.sqrt(o["var"]) * (precision != 0)
+
+
+def test_set_tile_rejects_bad_values(gv):
+    ctx = gv.vegas_create(wl.GENZ_GAUSSIAN, 3, wl.genz_gaussian_params(3), ncall=1000)
+    with ctx:
+        before = gv.vegas_get_tile(ctx)
+        for bad in (-1, 9):
+            with pytest.raises(gv.VegasError):
+                gv.vegas_set_tile(ctx, bad)
+        assert gv.vegas_get_tile(ctx) == before
