@@ -48,7 +48,7 @@ ALGO_OPS = {
 }
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/); None until captured for the current kernel.
-TRAFFIC = {"dgauss8": 54272}
+TRAFFIC = {"dgauss8": 68096}
 
 
 def _workload(name):
@@ -262,13 +262,17 @@ class Runner:
     @property
     def launches_per_step(self):
         w = self.w
+        # kernels of this library per step (memset nodes not counted):
+        # batched: one reset, then k_batch_sample + k_batch_finalize per
+        # iteration; BASES/VEGAS: grid reset (2), control (2), then
+        # k_sample + k_finish per pass; adjoint: k_grad + k_colsum
         if self.mode == "batched":
-            return 1 + 2 * sum(i["ndim"] for i in self.insts) + 2 * w["itmx"]
+            return 1 + 2 * w["itmx"]
         if self.mode == "bases":
-            return 2 + 2 + 3 * (w["itmx1"] + w["itmx2"])
+            return 2 + 2 + 2 * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return 2
-        return 2 + 2 + 3 * w["itmx"]
+        return 2 + 2 + 2 * w["itmx"]
 
     def step(self, h):
         gv, w = self.gv, self.w

@@ -316,14 +316,30 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
   }
 }
 
-__global__ void k_batch_reset(BatchState* st, int n, int reset_counter) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Whole-batch reset in one launch: block i clears instance i's state and
+// writes its uniform grid and both cell tables; block 0 also clears the
+// work-queue head.
+__global__ void k_batch_reset(BatchState* st, const BatchInst* inst, int n, int N, double* edges,
+                              double2* tab64, float2* tab32, int* head) {
+  const int i = blockIdx.x;
   if (i >= n) return;
-  st[i].nhist = 0;
-  st[i].nonfinite = 0;
-  st[i].samples = 0;
-  st[i].I = st[i].sigma = st[i].chi2 = 0.0;
-  if (reset_counter) st[i].it = 0;
+  if (threadIdx.x == 0) {
+    st[i].nhist = 0;
+    st[i].nonfinite = 0;
+    st[i].samples = 0;
+    st[i].I = st[i].sigma = st[i].chi2 = 0.0;
+    st[i].it = 0;
+    if (i == 0) *head = 0;
+  }
+  const BatchInst I = inst[i];
+  for (int j = threadIdx.x; j < I.d * (N + 1); j += blockDim.x)
+    edges[I.edge_off + j] = (double)(j % (N + 1)) / (double)N;
+  for (int j = threadIdx.x; j < I.d * N; j += blockDim.x) {
+    const int k = j % N;
+    const double lo = (double)k / (double)N, w = (double)(k + 1) / (double)N - lo;
+    tab64[I.tab_off + j] = make_double2(lo, w);
+    tab32[I.tab_off + j] = make_float2((float)lo, (float)w);
+  }
 }
 
 }  // namespace gv
@@ -758,14 +774,9 @@ vegas_status vegas_batch_iterate(vegas_batch* b, int n_iter, int refine, vegas_r
 
 vegas_status vegas_batch_reset(vegas_batch* b) {
   if (!b) return bfail("batch is NULL");
-  gv::k_batch_reset<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_st, b->n, 1);
+  gv::k_batch_reset<<<b->n, 128, 0, b->stream>>>(b->d_st, b->d_inst, b->n, b->N, b->d_edges, b->d_tab64,
+                                                   b->d_tab32, b->d_head);
   BK(b, cudaGetLastError());
-  for (int i = 0; i < b->n; ++i) {
-    const BatchInst& I = b->inst[i];
-    BK(b, gv_launch_uniform_grid(b->d_edges + I.edge_off, I.d, b->N, b->stream));
-    BK(b, gv_launch_tables(b->d_edges + I.edge_off, I.d, b->N, b->d_tab64 + I.tab_off, b->d_tab32 + I.tab_off,
-                           b->stream));
-  }
   return VEGAS_OK;
 }
 
