@@ -127,6 +127,48 @@ __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a
 __device__ __forceinline__ bool vfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool vfinite(float x) { return isfinite(x); }
 
+// Quick FP32 forms for the FP32 integrands: the special-function unit's
+// approximations (__logf, __expf, __sincosf, __fdividef, sqrt.approx),
+// a few parts in 2^22 on the ranges used; arguments of the trigonometric
+// forms are kept in [-pi, pi] by their callers.  The FP64 overloads are the
+// correctly rounded library functions, so FP64 kernels are unchanged.
+__device__ __forceinline__ float qlog(float x) { return __logf(x); }
+__device__ __forceinline__ double qlog(double x) { return log(x); }
+// ln x with a small relative error also near x = 1, where __logf's
+// absolute error would dominate a small result: 2 atanh(s),
+// s = (x - 1)/(x + 1), by its odd series through s^9 on [0.75, 1.25]
+// (|s| <= 1/7, truncation below 1e-8 relative), __logf elsewhere.
+__device__ __forceinline__ float qlog_rel(float x) {
+  const float s = __fdividef(x - 1.0f, x + 1.0f), s2 = s * s;
+  const float series =
+      2.0f * s * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
+  return (x > 0.75f && x < 1.25f) ? series : __logf(x);
+}
+__device__ __forceinline__ double qlog_rel(double x) { return log(x); }
+__device__ __forceinline__ float qexp(float x) { return __expf(x); }
+__device__ __forceinline__ double qexp(double x) { return exp(x); }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qsqrt(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qsin(float x) { return __sinf(x); }
+__device__ __forceinline__ double qsin(double x) { return sin(x); }
+__device__ __forceinline__ float qcos(float x) { return __cosf(x); }
+__device__ __forceinline__ double qcos(double x) { return cos(x); }
+// sin and cos of 2 pi u for u in [0, 1): evaluated at 2 pi (u - 1/2) in
+// [-pi, pi) and negated
+__device__ __forceinline__ void qsincos2pi(float u, float* s, float* c) {
+  float sn, cs;
+  __sincosf(6.28318530717958648f * (u - 0.5f), &sn, &cs);
+  *s = -sn;
+  *c = -cs;
+}
+__device__ __forceinline__ void qsincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };

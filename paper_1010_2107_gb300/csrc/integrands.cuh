@@ -15,6 +15,22 @@ namespace gv {
 __device__ __forceinline__ float gexp(float x) { return __expf(x); }
 __device__ __forceinline__ double gexp(double x) { return exp(x); }
 
+// t^e for t > 0: FP32 as exp(e ln t) on the quick forms, FP64 the library.
+__device__ __forceinline__ float qpow_pos(float t, float e) { return __expf(e * __logf(t)); }
+__device__ __forceinline__ double qpow_pos(double t, double e) { return pow(t, e); }
+
+// cos of a moderate argument: FP32 reduces to [-pi, pi] by r = t - k 2pi
+// with 2pi split in two floats (Cody and Waite): the fused multiply-add
+// subtracts k 2pi_hi with one rounding and k (2pi - 2pi_hi) corrects it,
+// before the quick form; FP64 the library.
+__device__ __forceinline__ float qcos_any(float t) {
+  const float k = rintf(t * 0.159154943091895336f);  // t / (2 pi)
+  // 2pi_hi = 6.28318548f exceeds 2pi by 1.7484555e-7
+  const float r = fmaf(k, 1.7484555e-7f, fmaf(-k, 6.28318548f, t));
+  return __cosf(r);
+}
+__device__ __forceinline__ double qcos_any(double t) { return cos(t); }
+
 // Derived-constant slots.  Genz / Gaussian: a-like values at [0, d),
 // u-like values at [kMaxDim, kMaxDim + d), raw a_i at [2 kMaxDim, ...),
 // scalars from kScalar on.
@@ -66,7 +82,7 @@ struct GenzProductPeak {
         const T t = x[a] - P[kMaxDim + a];
         den *= vfma(t, t, P[a]);
       }
-    return T(1) / den;
+    return qdiv(T(1), den);
   }
 };
 
@@ -78,7 +94,7 @@ struct GenzCornerPeak {
 #pragma unroll
     for (int a = 0; a < DM; ++a)
       if (a < d) t = vfma(P[a], x[a], t);
-    return vpow(t, P[kScalar]);
+    return qpow_pos(t, P[kScalar]);
   }
 };
 
@@ -90,7 +106,7 @@ struct GenzOscillatory {
 #pragma unroll
     for (int a = 0; a < DM; ++a)
       if (a < d) t = vfma(P[a], x[a], t);
-    return vcos(t);
+    return qcos_any(t);
   }
 };
 
@@ -143,8 +159,10 @@ struct DoubleGaussian {
 //   returns  cut * [mu_g / ((s12 - mu)^2 + mu_g^2)] * prod_i 1/s_{i,i+1}
 // (s_ij in units of s, mu = M^2/s, mu_g = M Gamma / s); the host multiplies
 // every sum by the constant V_n s^-3 (or the observable's own scale).
-// Invariants are formed as s_ij = 4 pT_i pT_j (sinh^2(deta/2) + sin^2(dphi/2)),
-// which has no cancellation for nearly collinear pairs in FP32.
+// Invariants are formed as s_ij = pT_i pT_j (4 sinh^2(deta/2) + |u_i - u_j|^2),
+// u the unit transverse direction (|u_i - u_j| = 2 sin(dphi/2)), which has no
+// cancellation for nearly collinear pairs in FP32 and needs no atan2.  The
+// FP32 kernels use the quick forms of common.cuh; FP64 the library.
 enum {
   RB_N = kScalar, RB_MU, RB_MUG, RB_MUG2, RB_PTMIN, RB_DR2, RB_CUT, RB_T,
   RB_INVWC, RB_OBS,
@@ -154,15 +172,31 @@ enum {
   RB_INVWC_GEV  // 1 / w_c                        (per GeV)
 };
 
+// sinh: FP32 through an odd Taylor polynomial below |x| = 1/2 (relative
+// error under 1e-8; exp(x) - exp(-x) would cancel there) and the quick
+// exponential above; FP64 through the library exponential.
+__device__ __forceinline__ float qsinh(float x) {
+  const float x2 = x * x;
+  const float poly = x * fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
+  const float e = __expf(x);
+  const float big = 0.5f * (e - __fdividef(1.0f, e));
+  return fabsf(x) < 0.5f ? poly : big;
+}
+__device__ __forceinline__ double qsinh(double x) {
+  const double e = exp(x);
+  return 0.5 * (e - 1.0 / e);
+}
+
 template <typename T, int DM>
 struct RamboBW {
   static constexpr int NM = DM / 4;
 
   struct Event {
-    T pt[NM], eta[NM], phi[NM];
+    T pt[NM], eta[NM], ux[NM], uy[NM];
   };
 
-  // Momenta -> (pT, eta, phi).  Returns false for a zero-weight point.
+  // Momenta -> (pT, eta, transverse direction).  Returns false for a
+  // zero-weight point.
   static __device__ __forceinline__ bool kinematics(const T (&x)[DM], int n, Event& ev) {
     T E[NM], px[NM], py[NM], pz[NM];
     T Q0 = T(0), Qx = T(0), Qy = T(0), Qz = T(0);
@@ -171,11 +205,11 @@ struct RamboBW {
       if (i < n) {
         const T r1 = x[4 * i], r2 = x[4 * i + 1], r3 = x[4 * i + 2], r4 = x[4 * i + 3];
         if (!(r1 > T(0) && r2 > T(0))) return false;
-        const T q0 = -(vlog(r1) + vlog(r2));
+        const T q0 = -(qlog_rel(r1) + qlog_rel(r2));
         const T c = T(2) * r3 - T(1);
-        const T sn = T(2) * vsqrt(r3 * (T(1) - r3));
+        const T sn = T(2) * qsqrt(r3 * (T(1) - r3));
         T sp, cp;
-        vsincospi(T(2) * r4, &sp, &cp);
+        qsincos2pi(r4, &sp, &cp);
         E[i] = q0;
         px[i] = q0 * sn * cp;
         py[i] = q0 * sn * sp;
@@ -185,11 +219,11 @@ struct RamboBW {
         Qy += py[i];
         Qz += pz[i];
       }
-    const T MQ = vsqrt((Q0 - Qz) * (Q0 + Qz) - Qx * Qx - Qy * Qy);
-    const T iM = T(1) / MQ;
+    const T MQ = qsqrt((Q0 - Qz) * (Q0 + Qz) - Qx * Qx - Qy * Qy);
+    const T iM = qdiv(T(1), MQ);
     const T bx = -Qx * iM, by = -Qy * iM, bz = -Qz * iM;
     const T gam = Q0 * iM;
-    const T A = T(1) / (T(1) + gam);
+    const T A = qdiv(T(1), T(1) + gam);
 #pragma unroll
     for (int i = 0; i < NM; ++i)
       if (i < n) {
@@ -199,33 +233,44 @@ struct RamboBW {
         const T qy = iM * vfma(ab, by, py[i]);
         const T qz = iM * vfma(ab, bz, pz[i]);
         const T pt2 = qx * qx + qy * qy;
-        const T pt = vsqrt(pt2);
-        const T pa = vsqrt(vfma(qz, qz, pt2));
+        const T pt = qsqrt(pt2);
+        const T pa = qsqrt(vfma(qz, qz, pt2));
+        const T ipt = qdiv(T(1), pt);
         ev.pt[i] = pt;
-        ev.eta[i] = vcopysign(vlog((fabs(qz) + pa) / pt), qz);
-        ev.phi[i] = vatan2(qy, qx);
+        ev.eta[i] = vcopysign(qlog_rel((fabs(qz) + pa) * ipt), qz);
+        ev.ux[i] = qx * ipt;
+        ev.uy[i] = qy * ipt;
       }
     return true;
   }
 
+  // |u_i - u_j|^2 = 4 sin^2(dphi / 2)
+  static __device__ __forceinline__ T chord2(const Event& ev, int i, int j) {
+    const T dx = ev.ux[i] - ev.ux[j], dy = ev.uy[i] - ev.uy[j];
+    return vfma(dx, dx, dy * dy);
+  }
+
   static __device__ __forceinline__ T sij(const Event& ev, int i, int j) {
-    const T he = T(0.5) * (ev.eta[i] - ev.eta[j]);
-    const T eh = vexp(he);
-    const T sh = T(0.5) * (eh - T(1) / eh);
-    const T sp = vsin(T(0.5) * (ev.phi[i] - ev.phi[j]));
-    return T(4) * ev.pt[i] * ev.pt[j] * vfma(sh, sh, sp * sp);
+    const T sh = qsinh(T(0.5) * (ev.eta[i] - ev.eta[j]));
+    return ev.pt[i] * ev.pt[j] * vfma(T(4) * sh, sh, chord2(ev, i, j));
   }
 
   static __device__ __forceinline__ T bw(T s12, const T* P) {
     const T t = s12 - P[RB_MU];
-    return P[RB_MUG] / vfma(t, t, P[RB_MUG2]);
+    return qdiv(P[RB_MUG], vfma(t, t, P[RB_MUG2]));
   }
 
-  static __device__ __forceinline__ T wrap_dphi(T dp) {
-    const T pi = T(3.14159265358979323846);
-    if (dp > pi) dp -= T(2) * pi;
-    if (dp < -pi) dp += T(2) * pi;
-    return dp;
+  // Delta R > R (pseudorapidity, dphi wrapped to [-pi, pi]): with
+  // t = R^2 - deta^2 > 0 the pair needs |dphi| > sqrt(t), i.e. sqrt(t) < pi
+  // and a chord |u_i - u_j| = 2 sin(|dphi|/2) beyond 2 sin(sqrt(t)/2).
+  static __device__ __forceinline__ bool dr_pass(const Event& ev, int i, int j, const T* P) {
+    const T de = ev.eta[i] - ev.eta[j];
+    const T t = P[RB_DR2] - de * de;
+    if (!(t > T(0))) return true;
+    const T th = qsqrt(t);
+    if (!(th < T(3.14159265358979323846))) return false;
+    const T h = qsin(T(0.5) * th);
+    return chord2(ev, i, j) > T(4) * h * h;
   }
 
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
@@ -243,18 +288,14 @@ struct RamboBW {
     } else if (obs == 0 && cut == 1) {
 #pragma unroll
       for (int i = 0; i < NM; ++i)
-        if (i < n) cw *= T(1) / (T(1) + vexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
+        if (i < n) cw *= qdiv(T(1), T(1) + qexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
     }
     if (obs == 0 && cut != 2) {
 #pragma unroll
       for (int i = 0; i < NM; ++i)
 #pragma unroll
         for (int j = i + 1; j < NM; ++j)
-          if (j < n) {
-            const T de = ev.eta[i] - ev.eta[j];
-            const T dp = wrap_dphi(ev.phi[i] - ev.phi[j]);
-            if (!(vfma(de, de, dp * dp) > P[RB_DR2])) return T(0);
-          }
+          if (j < n && !dr_pass(ev, i, j, P)) return T(0);
     }
     const T s12 = sij(ev, 0, 1);
     if (obs == 2) return s12;
@@ -264,7 +305,7 @@ struct RamboBW {
 #pragma unroll
     for (int i = 1; i < NM; ++i)
       if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
-    return cw * b / den;
+    return qdiv(cw * b, den);
   }
 
   // theta = (M, Gamma, T) in GeV for the full integrand (obs 0).  The Breit-
@@ -289,7 +330,7 @@ struct RamboBW {
 #pragma unroll
       for (int i = 0; i < NM; ++i)
         if (i < n) {
-          const T sg = T(1) / (T(1) + vexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
+          const T sg = qdiv(T(1), T(1) + qexp(-(ev.pt[i] - P[RB_T]) * P[RB_INVWC]));
           cw *= sg;
           dlc -= (T(1) - sg) * P[RB_INVWC_GEV];
         }
@@ -299,11 +340,7 @@ struct RamboBW {
       for (int i = 0; i < NM; ++i)
 #pragma unroll
         for (int j = i + 1; j < NM; ++j)
-          if (j < n) {
-            const T de = ev.eta[i] - ev.eta[j];
-            const T dp = wrap_dphi(ev.phi[i] - ev.phi[j]);
-            if (!(vfma(de, de, dp * dp) > P[RB_DR2])) return T(0);
-          }
+          if (j < n && !dr_pass(ev, i, j, P)) return T(0);
     }
     const T s12 = sij(ev, 0, 1);
     T den = s12;
@@ -312,13 +349,15 @@ struct RamboBW {
       if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
     const T t = s12 - P[RB_MU], mug = P[RB_MUG];
     const T D = vfma(t, t, P[RB_MUG2]);
-    const T b = mug / D;
-    const T pre = cw / den;
-    // db/dM = (mug' D - mug D') / D^2, D' = -2 t mu' + 2 mug mug'
-    const T dDdM = T(-2) * t * P[RB_DMU_DM] + T(2) * mug * P[RB_DMUG_DM];
-    const T dDdG = T(2) * mug * P[RB_DMUG_DG];
-    g[0] = pre * (P[RB_DMUG_DM] * D - mug * dDdM) / (D * D);
-    g[1] = pre * (P[RB_DMUG_DG] * D - mug * dDdG) / (D * D);
+    const T iD = qdiv(T(1), D);
+    const T b = mug * iD;
+    const T pre = qdiv(cw, den);
+    // db/dM = (mug' D - mug D') / D^2 with D' = -2 t mu' + 2 mug mug', whose
+    // numerator is mug' (t - mug)(t + mug) + 2 mug t mu' (no cancellation
+    // between mug' D and 2 mug^2 mug'); d/dGamma has mu' = 0.
+    const T tm = (t - mug) * (t + mug);
+    g[0] = pre * vfma(P[RB_DMUG_DM], tm, T(2) * mug * t * P[RB_DMU_DM]) * iD * iD;
+    g[1] = pre * (P[RB_DMUG_DG] * tm) * iD * iD;
     const T f = pre * b;
     g[2] = f * dlc;
     return f;
