@@ -80,14 +80,50 @@ struct BatchArgs {
 };
 
 // Integrand dispatch for the batch: the family is uniform over an item.
-template <typename T, int DM>
+// KIND >= 0 fixes it at compile time; -1 switches per point.
+template <int KIND, typename T, int DM>
 __device__ __forceinline__ T batch_eval(int kind, const T (&x)[DM], int d, const T* P) {
-  switch (kind) {
+  const int k = KIND >= 0 ? KIND : kind;
+  switch (k) {
     case VG_GENZ_GAUSSIAN: return GenzGaussian<T, DM>::eval(x, d, P);
     case VG_GENZ_PRODUCT_PEAK: return GenzProductPeak<T, DM>::eval(x, d, P);
     case VG_GENZ_CORNER_PEAK: return GenzCornerPeak<T, DM>::eval(x, d, P);
     case VG_GENZ_OSCILLATORY: return GenzOscillatory<T, DM>::eval(x, d, P);
     default: return DoubleGaussian<T, DM>::eval(x, d, P);
+  }
+}
+
+// The points of one work item (all threads of the CTA): DMC bounds the
+// instance's dimension, KIND its family (-1: decided per point).
+template <typename T, int ACC, int YB, int DMC, int KIND>
+__device__ __forceinline__ void batch_item_points(const BatchArgs& B, const SampleArgs& A, const BatchItem& W,
+                                                  int kind, uint32_t it, int d,
+                                                  const typename Vec2<T>::type* tab, const T* P,
+                                                  TileHist<ACC>& hist, Run<ACC>& sw, Run<ACC>& sw2,
+                                                  int& nonfinite) {
+  using H = typename AccTraits<ACC>::H;
+  int cd[DMC];
+#pragma unroll
+  for (int a = 0; a < DMC; ++a) cd[a] = 0;
+  const int tid = threadIdx.x;
+  const uint32_t rounds = (W.count + blockDim.x - 1) / blockDim.x;
+  for (uint32_t r = 0; r < rounds; ++r) {
+    const uint32_t j = r * blockDim.x + tid;
+    if (j < W.count) {
+      T x[DMC];
+      int kb[DMC];
+      const T J = make_point<T, DMC, YB>(A, it, W.s0 + j, cd, tab, x, kb, nullptr);
+      T w = batch_eval<KIND, T, DMC>(kind, x, d, P) * J;
+      if (!vfinite(w)) {
+        ++nonfinite;
+        w = T(0);
+      }
+      const H wh = (H)w;
+      sw.add(wh);
+      sw2.add(wh * wh);
+      hist.template scatter<DMC>(kb, d, wh);
+    }
+    if ((r + 1) % (uint32_t)B.ppt == 0 || r + 1 == rounds) hist.gather(tid, blockDim.x);
   }
 }
 
@@ -130,9 +166,6 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   for (int i = 0; i < kPhiloxKeyWords; ++i) A.ks[i] = B.ks[i];
   A.inv_gb_d = 1.0 / (double)(1ull << YB);
   A.inv_gb_f = (float)A.inv_gb_d;
-  int cd[DM];
-#pragma unroll
-  for (int a = 0; a < DM; ++a) cd[a] = 0;
   // one layout for every instance (sized for kBatchDM axes); the bucket
   // slots are cleared once and every gather leaves them cleared
   hist.bind(smem + L::hist(N), kBatchDM * N, N, B.cap, B.ppt, kBatchDM * N);
@@ -162,24 +195,17 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
     const uint32_t it = B.st[W.inst].it;
     Run<ACC> sw, sw2;
     int nonfinite = 0;
-    const uint32_t rounds = (W.count + blockDim.x - 1) / blockDim.x;
-    for (uint32_t r = 0; r < rounds; ++r) {
-      const uint32_t j = r * blockDim.x + tid;
-      if (j < W.count) {
-        T x[DM];
-        int kb[DM];
-        const T J = make_point<T, DM, YB>(A, it, W.s0 + j, cd, tab, x, kb, nullptr);
-        T w = batch_eval<T, DM>(I.kind, x, d, P) * J;
-        if (!vfinite(w)) {
-          ++nonfinite;
-          w = T(0);
-        }
-        const H wh = (H)w;
-        sw.add(wh);
-        sw2.add(wh * wh);
-        hist.template scatter<DM>(kb, d, wh);
-      }
-      if ((r + 1) % (uint32_t)B.ppt == 0 || r + 1 == rounds) hist.gather(tid, blockDim.x);
+    if constexpr (std::is_same<T, float>::value && YB == 24) {
+      // loops sized by the dimension class (d <= 4, <= 8, <= 16); a
+      // compile-time family as well would cost registers (measured)
+      if (d <= 4)
+        batch_item_points<T, ACC, YB, 4, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
+      else if (d <= 8)
+        batch_item_points<T, ACC, YB, 8, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
+      else
+        batch_item_points<T, ACC, YB, DM, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
+    } else {
+      batch_item_points<T, ACC, YB, DM, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
     }
     // the item's partial row: cells, then sum w, sum w^2, non-finite count
     for (int i = tid; i < 2 * dN; i += blockDim.x) {
