@@ -117,6 +117,31 @@ def _dist():
     return dist.get_rank(), dist.get_world_size(), int(os.environ.get("LOCAL_RANK", "0")), dist
 
 
+def max_over_ranks(x, dist):
+    """The largest value of x over all ranks (x itself on one rank): the
+    job's elapsed time is the slowest rank's."""
+    if not dist:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_step, steps, seconds):
+    """Units per second of the whole job: every rank processes
+    units_per_step per step (weak scaling), in the slowest rank's time."""
+    return world * units_per_step * steps / seconds
+
+
+def rank_instance(base, rank, mode):
+    """Philox instance word of a rank's replica: the context's instance is
+    the rank; a batch's instances are offset by 1024 per rank (a batch holds
+    fewer than 1024 instances), so no two ranks draw the same points."""
+    return base + 1024 * rank if mode == "batched" else rank
+
+
 def _cuda():
     import torch
     return torch.cuda.is_available()
@@ -222,7 +247,7 @@ class Runner:
             self.w = dict(wl.GENZ256)
             self.insts = wl.genz_batch(self.w["count"], self.w["seed"])
             for ins in self.insts:
-                ins["instance"] = ins["instance"] + 1024 * rank
+                ins["instance"] = rank_instance(ins["instance"], rank, "batched")
             self.mode = "batched"
         else:
             self.w = _workload(name)
@@ -242,8 +267,8 @@ class Runner:
             self.tuned = gv.vegas_batch_autotune(h)
             return h
         h = gv.vegas_create(w["kind"], w["ndim"], w["params"], nbins=w["nbins"], ncall=w["ncall"],
-                            nstrat=w["nstrat"], seed=w["seed"], instance=self.rank, precision=prec,
-                            ybits=w["ybits"], stream=self.stream)
+                            nstrat=w["nstrat"], seed=w["seed"], instance=rank_instance(0, self.rank, self.mode),
+                            precision=prec, ybits=w["ybits"], stream=self.stream)
         if self.mode == "adjoint":  # the grid the gradient is taken on
             gv.vegas_iterate(h, w["warmup_iters"], refine=True)
         return h
@@ -405,13 +430,9 @@ def run_ours(args):
     h = R.make(prec)
     with ClockSampler(local) as clk:
         step_ms = timed(h, args.steps, args.warmup)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist)
     pps = R.points_per_step
-    value = world * pps * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, pps, args.steps, total_ms / 1e3)
     res = R.result(h)
 
     # roofline of the dominant kernel, timed by CUDA events on its stream
@@ -460,12 +481,8 @@ def run_ours(args):
     for _ in range(ke):
         h2d, d2h = R.e2e_step(h)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * pps * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e = {"value": whole_job_rate(world, pps, ke, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": ke}
 
     cpu = None
