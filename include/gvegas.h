@@ -231,8 +231,10 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
                                double* x, double* jac, double* f);
 
 /* Launch shape of the sampling kernel: threads per CTA (multiple of 32,
- * 64..256) and CTAs per SM (0 = as many as fit).  Used by the autotuner;
- * takes effect on the next iteration.  EINVAL outside those ranges. */
+ * from 64 up to the kernel's limit: 512 for the specialised kernels, 256
+ * otherwise) and CTAs per SM (0 = as many as fit).  Used by the
+ * autotuner; takes effect on the next iteration.  EINVAL outside those
+ * ranges. */
 vegas_status vegas_set_launch(vegas_ctx* ctx, int threads, int ctas_per_sm);
 vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
                               int* ctas_per_sm);
@@ -248,6 +250,17 @@ vegas_status vegas_get_launch(vegas_ctx* ctx, int* threads, int* ctas,
  * shape then stays). */
 vegas_status vegas_set_tile(vegas_ctx* ctx, int points_per_thread);
 vegas_status vegas_get_tile(vegas_ctx* ctx, int* points_per_thread, int* cap);
+
+/* Launch-shape autotuner (the paper tunes nBlockSize by hand, Appendix A):
+ * times evaluation passes (as vegas_profile_pass: no refinement, window
+ * untouched) for threads per CTA in {128, 256, 384, 512} and histogram
+ * tiles in {automatic, 1, 2, 4} points per thread, skipping shapes the
+ * kernel cannot take, and keeps the fastest.  Returns its threads, points
+ * per thread and the pass time in ms (any output may be NULL).  The
+ * specialised kernels (d = the compiled bound, 24-bit words, power-of-two
+ * strata) accept up to 512 threads, the general ones 256.  Synchronises the
+ * stream. */
+vegas_status vegas_autotune(vegas_ctx* ctx, int* threads, int* points_per_thread, double* ms);
 
 /* Measurement (the paper times whole programs, Sec. 3.3; this times each
  * kernel): runs n_pass evaluation passes at the current iteration index

@@ -754,8 +754,10 @@ vegas_status vegas_sample_dump(vegas_ctx* c, uint32_t it, const uint64_t* s, int
 
 vegas_status vegas_set_launch(vegas_ctx* c, int threads, int ctas_per_sm) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  if (threads < 64 || threads > 256 || threads % 32 != 0)
-    return c->fail(VEGAS_EINVAL, "threads must be a multiple of 32 in 64..256");
+  cudaFuncAttributes fa{};
+  CK(c, cudaFuncGetAttributes(&fa, c->ke.sample));
+  if (threads < 64 || threads > fa.maxThreadsPerBlock || threads % 32 != 0)
+    return c->fail(VEGAS_EINVAL, "threads must be a multiple of 32 in 64..%d", fa.maxThreadsPerBlock);
   if (ctas_per_sm < 0) return c->fail(VEGAS_EINVAL, "ctas_per_sm < 0");
   CK(c, cudaStreamSynchronize(c->stream));
   const int t0 = c->threads, p0 = c->ctas_per_sm_req;
@@ -783,6 +785,36 @@ vegas_status vegas_set_tile(vegas_ctx* c, int points_per_thread) {
     configure_launch(c);
   }
   return st;
+}
+
+vegas_status vegas_autotune(vegas_ctx* c, int* threads, int* points_per_thread, double* ms) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  static const int kThreads[] = {128, 256, 384, 512};
+  static const int kTiles[] = {0, 1, 2, 4};
+  const int t0 = c->threads, p0 = c->ppt_req;
+  int best_t = t0, best_p = p0;
+  double best = 1e300;
+  for (int t : kThreads)
+    for (int p : kTiles) {
+      // shapes the kernel cannot take are skipped, not errors
+      if (vegas_set_launch(c, t, 0) != VEGAS_OK || vegas_set_tile(c, p) != VEGAS_OK) continue;
+      double m[3];
+      vegas_status st = vegas_profile_pass(c, 1, m);  // warm-up
+      if (!st) st = vegas_profile_pass(c, 3, m);
+      if (st) return st;
+      if (m[2] < best) {
+        best = m[2];
+        best_t = t;
+        best_p = p;
+      }
+    }
+  vegas_status st = vegas_set_launch(c, best_t, 0);
+  if (!st) st = vegas_set_tile(c, best_p);
+  if (st) return st;
+  if (threads) *threads = best_t;
+  if (points_per_thread) *points_per_thread = c->ppt;
+  if (ms) *ms = best;
+  return VEGAS_OK;
 }
 
 vegas_status vegas_get_tile(vegas_ctx* c, int* points_per_thread, int* cap) {

@@ -350,8 +350,14 @@ __device__ __forceinline__ fpair warp_sum(fpair p) {
   return p;
 }
 
+// Threads per CTA a sampling kernel may be launched with: the specialised
+// kernels up to 512 (larger tiles for many cells), the general ones 256
+// (their register budget).
+template <bool SPEC>
+constexpr int kSampleMaxThreads = SPEC ? 512 : 256;
+
 template <typename T, int DM, template <typename, int> class F, int ACC, int YB, bool SPEC>
-__global__ void __launch_bounds__(256) k_sample(const SampleArgs A) {
+__global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const SampleArgs A) {
   using H = typename AccTraits<ACC>::H;
   using T2 = typename Vec2<T>::type;
   using L = SmemLayout<T, ACC>;

@@ -85,6 +85,7 @@ _SIGS = {
     "vegas_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vegas_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
     "vegas_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_microbench": (ctypes.c_int, [ctypes.c_int, _DP]),
@@ -300,6 +301,13 @@ def vegas_get_launch(ctx: Context):
 
 def vegas_set_tile(ctx: Context, points_per_thread: int = 0):
     _check(lib().vegas_set_tile(ctx.handle, int(points_per_thread)), ctx.handle)
+
+
+def vegas_autotune(ctx: Context):
+    """Time the launch shapes and keep the fastest; returns the choice."""
+    t, p, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().vegas_autotune(ctx.handle, ctypes.byref(t), ctypes.byref(p), ctypes.byref(ms)), ctx.handle)
+    return dict(threads=t.value, points_per_thread=p.value, ms=ms.value)
 
 
 def vegas_get_tile(ctx: Context):

@@ -266,3 +266,39 @@ def test_set_tile_rejects_bad_values(gv):
             with pytest.raises(gv.VegasError):
                 gv.vegas_set_tile(ctx, bad)
         assert gv.vegas_get_tile(ctx) == before
+
+
+@pytest.mark.parametrize("nstrat", [0, 4])
+def test_autotuned_shape_keeps_parity(gv, orc, nstrat):
+    """The autotuner only changes the launch shape: the tuned context still
+    gives the oracle's sums."""
+    d, ncall = 8, 4 ** 8 * 3 + (0 if nstrat else 101)
+    params = wl.double_gaussian_params()
+    ctx, cfg, fn = _pair(gv, orc, wl.DOUBLE_GAUSSIAN, d, params, ncall=ncall, nstrat=nstrat, precision=2, ybits=24)
+    with ctx:
+        t = gv.vegas_autotune(ctx)
+        assert t["threads"] in (128, 256, 384, 512) and t["points_per_thread"] >= 1 and t["ms"] > 0
+        assert gv.vegas_get_launch(ctx)["threads"] == t["threads"]
+        I, var = gv.vegas_eval(ctx, 5)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 5)
+    p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 5, np.arange(ncall))
+    absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    assert _cond_close(bins[0], o["S1"], absw.sum(), 1e-5)
+    assert _cond_close(bins[1], o["S2"], (absw ** 2).sum(), 1e-5)
+    assert abs(I - o["I"]) <= 0.1 * math.sqrt(o["var"])
+
+
+def test_set_launch_limits(gv):
+    ctx = gv.vegas_create(wl.DOUBLE_GAUSSIAN, 8, wl.double_gaussian_params(), ncall=1 << 16, precision=2, ybits=24)
+    with ctx:
+        gv.vegas_set_launch(ctx, 512)  # specialised kernel: allowed
+        assert gv.vegas_get_launch(ctx)["threads"] == 512
+        for bad in (32, 100, 544, 1024):
+            with pytest.raises(gv.VegasError):
+                gv.vegas_set_launch(ctx, bad)
+        assert gv.vegas_get_launch(ctx)["threads"] == 512
+    ctx = gv.vegas_create(wl.DOUBLE_GAUSSIAN, 7, wl.double_gaussian_params(), ncall=1 << 16, precision=2, ybits=24)
+    with ctx:  # general kernel (d below the compiled bound): 256 at most
+        with pytest.raises(gv.VegasError):
+            gv.vegas_set_launch(ctx, 384)
