@@ -107,7 +107,13 @@ __device__ inline void refine_axis_core(const double* dd, double* ea, double2* t
   part = 0.0;
   for (int k = tid; k < N; k += t.n) {
     const double x = dsm[k];
-    const double rk = x <= 0.0 ? 0.0 : (x >= D ? 1.0 : pow((1.0 - x / D) / log(D / x), alpha));
+    double rk = x <= 0.0 ? 0.0 : 1.0;
+    if (x > 0.0 && x < D) {
+      // y^alpha; the default alpha = 3/2 as y sqrt(y) (a few FP64
+      // instructions instead of a general power)
+      const double y = (1.0 - x / D) / log(D / x);
+      rk = alpha == 1.5 ? y * sqrt(y) : pow(y, alpha);
+    }
     r[k] = rk;
     part += rk;
   }
