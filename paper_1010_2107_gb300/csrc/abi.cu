@@ -454,6 +454,7 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   if (c->ke.sample_spec && d == c->ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256) {
     c->ke.sample = c->ke.sample_spec;
     c->ppt_min = c->ke.spec_ppt_min;
+    if (c->ke.grad_spec) c->ke.grad = c->ke.grad_spec;
   }
   auto bail = [&](vegas_status st) {
     g_thread_err = c->err;

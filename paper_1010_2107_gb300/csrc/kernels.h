@@ -24,6 +24,7 @@ struct KernelEntry {
   int spec_ppt_min;                   // `sample_spec` evaluates this many points per
                                       // thread at a time: tiles are multiples of it
   const void* grad;                   // k_grad<T, DM, F, YB> or null
+  const void* grad_spec;              // k_grad<T, DM, F, 24, true> (specialised shape) or null
   int grad_nt;                        // its gradient columns (F<T, DM>::NT)
   size_t (*grad_smem)(int d, int N);
 };

@@ -704,13 +704,14 @@ template <> struct HasGrad<GenzGaussian> { static constexpr bool value = true; }
 template <> struct HasGrad<DoubleGaussian> { static constexpr bool value = true; };
 template <> struct HasGrad<RamboBW> { static constexpr bool value = true; };
 
-template <typename T, int DM, template <typename, int> class F, int YB>
+template <typename T, int DM, template <typename, int> class F, int YB, bool SPEC = false>
 __global__ void __launch_bounds__(256) k_grad(const SampleArgs A, double* part) {
   using T2 = typename Vec2<T>::type;
   constexpr int NT = F<T, DM>::NT;
   constexpr int NC = NT + 2;
   constexpr bool F32 = std::is_same<T, float>::value;
-  const int d = A.d, N = A.N, dN = d * N;
+  // SPEC: d equals DM, 24-bit words, power-of-two divisions (as k_sample)
+  const int d = SPEC ? DM : A.d, N = A.N, dN = d * N;
   const uint32_t it = (uint32_t)A.it_override;
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
@@ -736,13 +737,18 @@ __global__ void __launch_bounds__(256) k_grad(const SampleArgs A, double* part) 
     for (int a = 0; a < DM; ++a) {
       cd[a] = 0;
       if (a < d && A.strat) {
-        cd[a] = (int)(rest % (uint32_t)A.g);
-        rest /= (uint32_t)A.g;
+        if (SPEC) {
+          cd[a] = (int)(rest & (uint32_t)(A.g - 1));
+          rest >>= A.g_log2;
+        } else {
+          cd[a] = (int)(rest % (uint32_t)A.g);
+          rest /= (uint32_t)A.g;
+        }
       }
     }
     T x[DM];
     int kb[DM];
-    const T J = make_point<T, DM, YB>(A, it, (uint32_t)s, cd, tab, x, kb, nullptr);
+    const T J = make_point<T, DM, YB, SPEC>(A, it, (uint32_t)s, cd, tab, x, kb, nullptr);
     T g[NT];
 #pragma unroll
     for (int q = 0; q < NT; ++q) g[q] = T(0);
@@ -797,10 +803,15 @@ template <typename T, int DM, template <typename, int> class F, int YB>
 inline void grad_entry(KernelEntry& e) {
   if constexpr (HasGrad<F>::value && (DM <= 20)) {
     e.grad = (const void*)&k_grad<T, DM, F, YB>;
+    if constexpr (YB == 24)
+      e.grad_spec = (const void*)&k_grad<T, DM, F, 24, true>;
+    else
+      e.grad_spec = nullptr;
     e.grad_nt = F<T, DM>::NT;
     e.grad_smem = &grad_smem_bytes<T>;
   } else {
     e.grad = nullptr;
+    e.grad_spec = nullptr;
     e.grad_nt = 0;
     e.grad_smem = nullptr;
   }
