@@ -170,6 +170,40 @@ def oracle_rate(name: str, iters_refine: int, iters_frozen: int):
     return n / dt, n, dt
 
 
+def _oracle_worker(job):
+    """One process of the all-core CPU baseline: the oracle on its own
+    instance word (a disjoint Philox counter range), timed inside."""
+    name, instance = job
+    import oracle
+    oracle.build()
+    w = _workload(name)
+    d = w["ndim"]
+    cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
+                          seed=w["seed"], instance=instance)
+    fn = oracle.Integrand(w["kind"], d, w["params"])
+    oracle.vegas(cfg, fn, oracle.uniform_grid(d, w["nbins"]), 0, 1)  # untimed warm-up
+    e = oracle.uniform_grid(d, w["nbins"])
+    t = time.perf_counter()
+    oracle.vegas(cfg, fn, e, 0, 1)
+    return w["ncall"], time.perf_counter() - t
+
+
+def oracle_rate_allcores(name: str):
+    """The oracle as it stands, one full-NCALL iteration in each of P
+    independent processes (P = the cores this process may use), each on
+    disjoint counter ranges: points of all processes over the slowest
+    process's time.  Spawned processes (no fork after CUDA is up)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    P = len(os.sched_getaffinity(0))
+    # a worker that dies makes the executor raise instead of waiting forever
+    with ProcessPoolExecutor(max_workers=P, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_worker, [(name, 1 + p) for p in range(P)], timeout=600))
+    n = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return n / dt, n, dt, P
+
+
 def run_reference(args):
     rank, world, _, dist = _dist()
     if rank != 0:
@@ -490,13 +524,20 @@ def run_ours(args):
     e2e = {"value": whole_job_rate(world, pps, ke, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": ke}
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu and R.mode in ("bases", "vegas"):
         bases = R.mode == "bases"
         rate, n, dt = oracle_rate(args.workload, 3, 3) if bases else oracle_rate(args.workload, 1, 0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} points: full-NCALL iterations of the same workload "
                          f"({'3+3 BASES' if bases else '1 VEGAS'}), {dt:.1f} s single-threaded FP64 C oracle"}
+        try:
+            rate_p, n_p, dt_p, P = oracle_rate_allcores(args.workload)
+            cpu_all = {"value": rate_p, "unit": UNIT, "cores": P, "kind": "oracle, one process per core",
+                       "sample": f"{n_p} points: one full-NCALL iteration in each of {P} processes on "
+                                 f"disjoint counter ranges, slowest {dt_p:.1f} s"}
+        except Exception as e:  # the single-threaded line above stands on its own
+            cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
 
     clocks = clk.summary()
     if rank == 0:
@@ -507,6 +548,7 @@ def run_ours(args):
             "data": "synthetic", "config": dict(_config(args.workload), accumulation=R.prec_name,
                                                 launch=R.launch(h)),
             "roofline": roof, **extra, "fp64_path": fp64, "cpu_baseline": cpu,
+            "cpu_baseline_allcores": cpu_all,
             "e2e": e2e, "gpu_launches": R.launches_per_step * args.steps, "clocks": clocks,
             "result": res,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
