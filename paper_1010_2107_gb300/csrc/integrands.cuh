@@ -43,16 +43,37 @@ constexpr int kScalar = 3 * kMaxDim;
 
 // ----------------------------------------------------------------- Genz
 // f = exp(-sum a_i^2 (x_i - u_i)^2).  P[i] = a_i^2, P[kMaxDim+i] = u_i.
+// FP32 pairs of consecutive axes for the paired FP32 instructions: x[a],
+// x[a+1] (the second replaced by `pad` past d) and the constants P[o + a],
+// P[o + a + 1] (8-byte aligned: o and a even).
+template <int DM>
+__device__ __forceinline__ float2 xpair(const float (&x)[DM], int a, int d, float pad) {
+  return make_float2(x[a], a + 1 < d ? x[a + 1] : pad);
+}
+__device__ __forceinline__ float2 ppair(const float* P, int i) { return *reinterpret_cast<const float2*>(P + i); }
+
 template <typename T, int DM>
 struct GenzGaussian {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     T q = T(0);
+    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
+      float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) {
-        const T t = x[a] - P[kMaxDim + a];
-        q = vfma(P[a] * t, t, q);
-      }
+      for (int a = 0; a < DM; a += 2)
+        if (a < d) {
+          const float2 u = ppair(P, kMaxDim + a);
+          const float2 t = __fadd2_rn(xpair(x, a, d, u.y), make_float2(-u.x, -u.y));
+          s = __ffma2_rn(__fmul2_rn(ppair(P, a), t), t, s);
+        }
+      q = s.x + s.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DM; ++a)
+        if (a < d) {
+          const T t = x[a] - P[kMaxDim + a];
+          q = vfma(P[a] * t, t, q);
+        }
+    }
     return gexp(-q);
   }
   // theta = (u_1..u_d, a_1..a_d): df/du_i = 2 a_i^2 (x_i - u_i) f,
@@ -76,12 +97,25 @@ template <typename T, int DM>
 struct GenzProductPeak {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     T den = T(1);
+    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
+      float2 dd = make_float2(1.f, 1.f);
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) {
-        const T t = x[a] - P[kMaxDim + a];
-        den *= vfma(t, t, P[a]);
-      }
+      for (int a = 0; a < DM; a += 2)
+        if (a < d) {
+          const float2 u = ppair(P, kMaxDim + a), c = ppair(P, a);
+          // past d: t = 0 and the factor c.y replaced by 1
+          const float2 t = __fadd2_rn(xpair(x, a, d, u.y), make_float2(-u.x, -u.y));
+          dd = __fmul2_rn(dd, __ffma2_rn(t, t, make_float2(c.x, a + 1 < d ? c.y : 1.f)));
+        }
+      den = dd.x * dd.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DM; ++a)
+        if (a < d) {
+          const T t = x[a] - P[kMaxDim + a];
+          den *= vfma(t, t, P[a]);
+        }
+    }
     return qdiv(T(1), den);
   }
 };
@@ -91,9 +125,17 @@ template <typename T, int DM>
 struct GenzCornerPeak {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     T t = T(1);
+    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
+      float2 s = make_float2(1.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) t = vfma(P[a], x[a], t);
+      for (int a = 0; a < DM; a += 2)
+        if (a < d) s = __ffma2_rn(ppair(P, a), xpair(x, a, d, 0.f), s);
+      t = s.x + s.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DM; ++a)
+        if (a < d) t = vfma(P[a], x[a], t);
+    }
     return qpow_pos(t, P[kScalar]);
   }
 };
@@ -103,9 +145,17 @@ template <typename T, int DM>
 struct GenzOscillatory {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     T t = P[kScalar];
+    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
+      float2 s = make_float2(P[kScalar], 0.f);
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) t = vfma(P[a], x[a], t);
+      for (int a = 0; a < DM; a += 2)
+        if (a < d) s = __ffma2_rn(ppair(P, a), xpair(x, a, d, 0.f), s);
+      t = s.x + s.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DM; ++a)
+        if (a < d) t = vfma(P[a], x[a], t);
+    }
     return qcos_any(t);
   }
 };
@@ -118,13 +168,31 @@ struct DoubleGaussian {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     const T c1 = P[kScalar], c2 = P[kScalar + 1];
     T q1 = T(0), q2 = T(0);
+    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
+      // two axes per paired FP32 instruction (FADD2 / FFMA2); an axis past
+      // d contributes nothing
+      float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+      const float2 m1 = make_float2(-c1, -c1), m2 = make_float2(-c2, -c2);
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) {
-        const T t1 = x[a] - c1, t2 = x[a] - c2;
-        q1 = vfma(t1, t1, q1);
-        q2 = vfma(t2, t2, q2);
-      }
+      for (int a = 0; a < DM; a += 2)
+        if (a < d) {
+          const float2 xa = make_float2(x[a], a + 1 < d ? x[a + 1] : c1);
+          const float2 xb = make_float2(x[a], a + 1 < d ? x[a + 1] : c2);
+          const float2 t1 = __fadd2_rn(xa, m1), t2 = __fadd2_rn(xb, m2);
+          s1 = __ffma2_rn(t1, t1, s1);
+          s2 = __ffma2_rn(t2, t2, s2);
+        }
+      q1 = s1.x + s1.y;
+      q2 = s2.x + s2.y;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DM; ++a)
+        if (a < d) {
+          const T t1 = x[a] - c1, t2 = x[a] - c2;
+          q1 = vfma(t1, t1, q1);
+          q2 = vfma(t2, t2, q2);
+        }
+    }
     const T iw2 = P[kScalar + 2];
     return P[kScalar + 3] * (gexp(-q1 * iw2) + gexp(-q2 * iw2));
   }

@@ -654,7 +654,7 @@ inline size_t sample_smem_bytes(int d, int N, int cap) {
 // the Philox words, bins, point, Jacobian and integrand value of each.
 template <typename T, int DM, template <typename, int> class F, int YB>
 __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
-  __shared__ T P[kNumDerived];
+  __shared__ __align__(16) T P[kNumDerived];  // paired loads read 8-byte pairs
   for (int i = threadIdx.x; i < kNumDerived; i += blockDim.x) P[i] = (T)D.S.dparams[i];
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
