@@ -69,7 +69,8 @@ class IterOut(ctypes.Structure):
                 ("C1", ctypes.POINTER(ctypes.c_double)),
                 ("C2", ctypes.POINTER(ctypes.c_double)),
                 ("tot", ctypes.c_double * 4),
-                ("nonfinite", ctypes.c_int64)]
+                ("nonfinite", ctypes.c_int64),
+                ("Cmax", ctypes.POINTER(ctypes.c_double))]
 
 
 def lib():
@@ -217,12 +218,13 @@ def iteration(cfg: Cfg, fn: Integrand, edges, it: int, cubes: bool = False):
     S2 = np.zeros((d, N))
     out = IterOut()
     out.S1, out.S2 = _dp(S1), _dp(S2)
-    C1 = C2 = None
+    C1 = C2 = Cmax = None
     if cubes:
         g = max(cfg.nstrat, 1)
         C1 = np.zeros(g ** d)
         C2 = np.zeros(g ** d)
-        out.C1, out.C2 = _dp(C1), _dp(C2)
+        Cmax = np.zeros(g ** d)
+        out.C1, out.C2, out.Cmax = _dp(C1), _dp(C2), _dp(Cmax)
     edges = np.ascontiguousarray(edges, dtype=np.float64)
     if lib().orc_iteration(ctypes.byref(cfg), fn.fn, _dp(edges), ctypes.c_uint32(it),
                            ctypes.byref(out)):
@@ -230,8 +232,36 @@ def iteration(cfg: Cfg, fn: Integrand, edges, it: int, cubes: bool = False):
     res = dict(S1=S1, S2=S2, sum_w=out.tot[0], sum_w2=out.tot[1], I=out.tot[2],
                var=out.tot[3], nonfinite=out.nonfinite)
     if cubes:
-        res.update(C1=C1, C2=C2)
+        res.update(C1=C1, C2=C2, Cmax=Cmax)
     return res
+
+
+def spring_table(cmax):
+    """Integer hypercube weights q_c and the scale 2^24 / max M (SPRING)."""
+    cmax = np.ascontiguousarray(cmax, dtype=np.float64)
+    q = np.zeros(len(cmax), dtype=np.uint64)
+    scale = ctypes.c_double()
+    if lib().orc_spring_table(ctypes.c_int64(len(cmax)), _dp(cmax),
+                              q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(scale)):
+        raise ValueError("orc_spring_table: no positive maximum")
+    return q, scale.value
+
+
+def spring(cfg: Cfg, fn: Integrand, edges, cmax, t0: int, n: int):
+    """SPRING trials t0 .. t0+n-1 on a frozen grid with per-cube maxima cmax;
+    returns kept points x [k][ndim], their trial indices, and the numbers of
+    bound overflows and non-positive weights."""
+    d = cfg.ndim
+    x = np.zeros((n, d))
+    t = np.zeros(n, dtype=np.uint64)
+    k, ov, npos = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    cmax = np.ascontiguousarray(cmax, dtype=np.float64)
+    if lib().orc_spring(ctypes.byref(cfg), fn.fn, _dp(edges), _dp(cmax), ctypes.c_uint64(t0),
+                        ctypes.c_int64(n), _dp(x), t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                        ctypes.byref(k), ctypes.byref(ov), ctypes.byref(npos)):
+        raise ValueError("orc_spring failed")
+    return dict(x=x[:k.value], trial=t[:k.value], overflow=ov.value, nonpos=npos.value)
 
 
 def refine(S2, edges, alpha=1.5) -> np.ndarray:

@@ -487,6 +487,7 @@ int orc_iteration(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
   }
   ksum tw = {0, 0}, tw2 = {0, 0}, tI = {0, 0}, tV = {0, 0};
   ksum cw = {0, 0}, cw2 = {0, 0};
+  double cmax = 0.0;
   int32_t bins[ORC_MAXDIM];
   double x[ORC_MAXDIM], J;
   out->nonfinite = 0;
@@ -505,6 +506,11 @@ int orc_iteration(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
     }
     kadd(&tw, w);
     kadd(&tw2, w2);
+    if (w > cmax) cmax = w;
+    if (out->Cmax && (s + 1) % nc == 0) {
+      out->Cmax[s / nc] = cmax;
+      cmax = 0.0;
+    }
     if (strat) {
       kadd(&cw, w);
       kadd(&cw2, w2);
@@ -684,6 +690,117 @@ int orc_bases(const orc_cfg* cfg, const orc_fn* fn, double* edges,
   n_done[0] = n1;
   n_done[1] = n2;
   return n1 + n2;
+}
+
+/* ------------------------------------------------------------------ */
+/* SPRING: unweighted events on the frozen grid of the BASES           */
+/* integration phase (see oracle.h for the reading).                   */
+/* ------------------------------------------------------------------ */
+
+#define ORC_SPRING_IT 0xFFFFFFFFu
+
+int orc_spring_table(int64_t G, const double* cmax, uint64_t* q, double* scale) {
+  double mx = 0.0;
+  for (int64_t c = 0; c < G; ++c)
+    if (cmax[c] > mx) mx = cmax[c];
+  if (!(mx > 0.0) || !isfinite(mx)) return -1;
+  *scale = 16777216.0 / mx; /* 2^24 / max M */
+  for (int64_t c = 0; c < G; ++c) {
+    double v = cmax[c] > 0.0 ? ceil(cmax[c] * *scale) : 0.0;
+    q[c] = (uint64_t)v;
+  }
+  return 0;
+}
+
+/* floor(U Q / 2^64) in 64-bit pieces: U Q = (Uh 2^32 + Ul)(Qh 2^32 + Ql). */
+static uint64_t mul_hi64(uint64_t U, uint64_t Q) {
+  uint64_t Uh = U >> 32, Ul = U & 0xFFFFFFFFull;
+  uint64_t Qh = Q >> 32, Ql = Q & 0xFFFFFFFFull;
+  uint64_t ll = Ul * Ql, lh = Ul * Qh, hl = Uh * Ql, hh = Uh * Qh;
+  uint64_t mid = (ll >> 32) + (lh & 0xFFFFFFFFull) + (hl & 0xFFFFFFFFull);
+  return hh + (lh >> 32) + (hl >> 32) + (mid >> 32);
+}
+
+int orc_spring(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
+               const double* cmax, uint64_t t0, int64_t n, double* x_out,
+               uint64_t* trial_out, int64_t* n_events, int64_t* overflow,
+               int64_t* nonpos) {
+  if (!cfg_valid(cfg) || !fn_valid(fn) || fn->ndim != cfg->ndim) return -1;
+  if (n < 0 || t0 + (uint64_t)n > 0x100000000ull) return -1;
+  int d = cfg->ndim, W = words_per_sample(cfg), V = cfg->ybits == 24 ? 1 : 2;
+  int64_t G = n_cubes(cfg);
+  if (G < 0) return -1;
+  uint64_t* q = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)G);
+  uint64_t* P = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(G + 1));
+  if (!q || !P) {
+    free(q);
+    free(P);
+    return -1;
+  }
+  double scale;
+  if (orc_spring_table(G, cmax, q, &scale)) {
+    free(q);
+    free(P);
+    return -1;
+  }
+  P[0] = 0;
+  for (int64_t c = 0; c < G; ++c) P[c + 1] = P[c] + q[c];
+  uint64_t Q = P[G];
+  uint32_t key[2] = {(uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32)};
+  uint32_t w[2 * ORC_MAXDIM + 8];
+  int nw = W + 2 + V;
+  int64_t k = 0, ov = 0, np = 0;
+  double x[ORC_MAXDIM], J;
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t t = t0 + (uint64_t)i;
+    for (int g4 = 0; 4 * g4 < nw; ++g4) {
+      uint32_t ctr[4] = {(uint32_t)t, (uint32_t)g4, ORC_SPRING_IT, cfg->instance};
+      uint32_t out[4];
+      orc_philox4x32_10(ctr, key, out);
+      for (int r = 0; r < 4 && 4 * g4 + r < nw; ++r) w[4 * g4 + r] = out[r];
+    }
+    /* the cube: the last c with P[c] <= u, by bisection over P[0..G] */
+    uint64_t U = ((uint64_t)w[W] << 32) | (uint64_t)w[W + 1];
+    uint64_t u = mul_hi64(U, Q);
+    int64_t lo = 0, hi = G; /* P[lo] <= u < P[hi] */
+    while (hi - lo > 1) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (P[mid] <= u)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    int64_t c = lo;
+    orc_point_from_words(cfg, edges, (uint64_t)c, w, NULL, NULL, x, &J);
+    double f = eval_point(fn, x, NULL);
+    double wt = f * J;
+    double v = V == 1 ? (double)(w[W + 2] >> 8) / 16777216.0
+                      : ((double)(w[W + 2] >> 5) * 67108864.0 + (double)(w[W + 3] >> 6)) /
+                            9007199254740992.0;
+    double Mt = (double)q[c] / scale;
+    int keep;
+    if (!(wt > 0.0)) {
+      ++np;
+      keep = 0;
+    } else if (wt > Mt) {
+      ++ov;
+      keep = 1;
+    } else {
+      keep = v * Mt < wt;
+    }
+    if (keep) {
+      if (x_out)
+        for (int a = 0; a < d; ++a) x_out[(size_t)k * d + a] = x[a];
+      if (trial_out) trial_out[k] = t;
+      ++k;
+    }
+  }
+  free(q);
+  free(P);
+  *n_events = k;
+  if (overflow) *overflow = ov;
+  if (nonpos) *nonpos = np;
+  return 0;
 }
 
 /* Gradient of the iteration estimate with respect to integrand

@@ -81,7 +81,8 @@ typedef struct {
 } orc_cfg;
 
 /* Per-iteration outputs.  S1, S2: [ndim][nbins]; C1, C2: [nstrat^ndim]
- * (may be NULL).  tot: {sum w, sum w^2, I_j, sigma_j^2}. */
+ * (may be NULL).  tot: {sum w, sum w^2, I_j, sigma_j^2}.  Cmax (may be
+ * NULL): [nstrat^ndim], per hypercube max(0, largest w), for SPRING. */
 typedef struct {
   double* S1;
   double* S2;
@@ -89,6 +90,7 @@ typedef struct {
   double* C2;
   double tot[4];
   int64_t nonfinite;
+  double* Cmax;
 } orc_iter_out;
 
 /* Philox4x32-10 block: out = Philox(ctr, key). */
@@ -158,6 +160,26 @@ int orc_vegas(const orc_cfg* cfg, const orc_fn* fn, double* edges,
 int orc_bases(const orc_cfg* cfg, const orc_fn* fn, double* edges,
               uint32_t it0, int itmx1, double acc1, int itmx2, double acc2,
               double* hist, double out[3], int n_done[2]);
+
+/* SPRING (unweighted events from the BASES integration phase; Sec. 2.1
+ * names it, Kawabata's BASES/SPRING defines it; the steps below are this
+ * build's reading).  orc_spring_table: integer hypercube weights
+ * q_c = ceil(M_c * scale), scale = 2^24 / max_c M_c, from the per-cube
+ * maxima M_c; returns -1 when every M_c is 0.  orc_spring: trials
+ * t = t0 .. t0 + n - 1, each from the Philox words of counter
+ * (t, word group, 0xFFFFFFFF, instance): words 0..W-1 place a point in the
+ * chosen cube as the sampling step does (W = ndim, or 2 ndim for 53-bit
+ * words), words W and W+1 form U = 2^32 w_W + w_{W+1} and pick the cube c
+ * with P_c <= floor(U Q / 2^64) < P_{c+1} (P the prefix sums of q, Q the
+ * total), and the next word (two for 53-bit) gives v in [0, 1).  With
+ * w = f J and Mt = q_c / scale: w <= 0 is dropped (*nonpos), w > Mt is kept
+ * (*overflow), otherwise kept iff v Mt < w.  Kept points go to x_out[k][ndim]
+ * and trial_out[k] in trial order; *n_events = k. */
+int orc_spring_table(int64_t G, const double* cmax, uint64_t* q, double* scale);
+int orc_spring(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
+               const double* cmax, uint64_t t0, int64_t n, double* x_out,
+               uint64_t* trial_out, int64_t* n_events, int64_t* overflow,
+               int64_t* nonpos);
 
 /* Estimator gradient on a frozen grid: dI/dtheta = (1/n) sum J df/dtheta. */
 int orc_gradient(const orc_cfg* cfg, const orc_fn* fn, const double* edges,
