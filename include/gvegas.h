@@ -230,6 +230,28 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
                                int64_t n, uint32_t* words, int32_t* bins,
                                double* x, double* jac, double* f);
 
+/* SPRING (Sec. 2.1: the results of the BASES integration phase drive event
+ * generation; the steps are Kawabata's SPRING as this build reads them).
+ * Every bases_integrate records, during its integration phase, the largest
+ * weight M_c = max(0, f J) seen in each hypercube c.
+ * vegas_get_cube_max copies those maxima (in the integrand's units, like
+ * vegas_get_cube_sums; G = nstrat^ndim values, 1 without stratification).
+ * spring_generate runs trials t = trial0 .. trial0 + n_trials - 1 on the
+ * frozen grid: each picks cube c with probability q_c / Q, q_c =
+ * ceil(M_c 2^24 / max M) (Q the sum), places a point in it as the sampling
+ * step does, and keeps it with probability w / (q_c max M 2^-24); a weight
+ * above that bound is kept and counted in *n_overflow, a non-positive one
+ * dropped and counted in *n_nonpos.  The Philox words of trial t come from
+ * counter (t, word group, 0xFFFFFFFF, instance).  Kept points go to
+ * x_out[k][ndim] and trial_out[k] (host arrays with room for n_trials rows;
+ * either may be NULL to leave the events on the device) in trial order;
+ * *n_events = k.  VEGAS_ESTATE before any bases_integrate or when every
+ * maximum is zero; EINVAL when trial0 + n_trials exceeds 2^32. */
+vegas_status vegas_get_cube_max(vegas_ctx* ctx, double* cmax);
+vegas_status spring_generate(vegas_ctx* ctx, uint64_t trial0, uint32_t n_trials,
+                             double* x_out, uint64_t* trial_out, uint32_t* n_events,
+                             uint32_t* n_overflow, uint32_t* n_nonpos);
+
 /* Launch shape of the sampling kernel: threads per CTA (multiple of 32,
  * from 64 up to the kernel's limit: 512 for the specialised kernels, 256
  * otherwise) and CTAs per SM (0 = as many as fit).  Used by the

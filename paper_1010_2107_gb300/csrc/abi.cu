@@ -63,6 +63,19 @@ struct vegas_ctx {
   double* d_bins = nullptr;
   double* d_tot = nullptr;
   double* d_cubes = nullptr;
+  double* d_cube_max = nullptr;  // [G] max(0, largest w) per cube, integration phase
+  bool have_max = false;         // a bases_integrate has recorded the maxima
+  // SPRING buffers (grown on demand)
+  uint64_t* d_q = nullptr;
+  uint64_t* d_prefix = nullptr;
+  double* d_meta = nullptr;        // {Q, scale, status}
+  double* d_stage_x = nullptr;     // [n][d]
+  uint64_t* d_stage_t = nullptr;   // [n]
+  double* d_out_x = nullptr;
+  uint64_t* d_out_t = nullptr;
+  uint32_t* d_counts = nullptr;
+  unsigned long long* d_counters = nullptr;
+  uint32_t spring_cap = 0, spring_chunks_cap = 0;
   double* d_gpart = nullptr;  // adjoint partials [grad_nt + 2][grad_ctas] then totals
   int grad_ctas = 0;
   size_t grad_smem = 0;
@@ -133,6 +146,80 @@ void destroy_graphs(vegas_ctx* c) {
 
 // Launch geometry: a persistent grid of CTAs per SM as occupancy allows
 // (or as requested), capped by the work available.
+// SPRING table (one block): M = largest recorded maximum (after the output
+// scale); scale = 2^24 / M; q_c = ceil(M_c scale) in FP64 as the oracle
+// computes it; exclusive prefix sums P[0..G] in 64-bit integers.  meta:
+// {Q, scale, status} (status 1: no positive maximum).
+__global__ void k_spring_table(const double* cmax, uint32_t G, double out_scale, uint64_t* q, uint64_t* prefix,
+                               double* meta) {
+  __shared__ double smax[32];
+  __shared__ unsigned long long ssum[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double m = 0.0;
+  for (uint32_t i = tid; i < G; i += nt) m = fmax(m, cmax[i] * out_scale);
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((tid & 31) == 0) smax[tid >> 5] = m;
+  __syncthreads();
+  double M = 0.0;
+  for (int w = 0; w < nt / 32; ++w) M = fmax(M, smax[w]);
+  if (!(M > 0.0) || !isfinite(M)) {
+    if (tid == 0) {
+      meta[0] = 0.0;
+      meta[1] = 0.0;
+      meta[2] = 1.0;
+    }
+    return;
+  }
+  const double scale = 16777216.0 / M;
+  const uint32_t per = (G + nt - 1) / nt, lo = min((uint32_t)tid * per, G), hi = min(lo + per, G);
+  unsigned long long sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const double v = cmax[i] * out_scale;
+    const uint64_t qi = v > 0.0 ? (uint64_t)ceil(v * scale) : 0ull;
+    q[i] = qi;
+    sum += qi;
+  }
+  ssum[tid] = sum;
+  __syncthreads();
+  if (tid == 0) {  // exclusive scan of the thread sums (integers: any order is exact)
+    unsigned long long run = 0;
+    for (int k = 0; k < nt; ++k) {
+      const unsigned long long v = ssum[k];
+      ssum[k] = run;
+      run += v;
+    }
+    prefix[G] = run;
+    meta[0] = (double)run;
+    meta[1] = scale;
+    meta[2] = 0.0;
+  }
+  __syncthreads();
+  unsigned long long run = ssum[tid];
+  for (uint32_t i = lo; i < hi; ++i) {
+    prefix[i] = run;
+    run += q[i];
+  }
+}
+
+// SPRING compaction: block k copies chunk k's kept points behind those of
+// chunks 0 .. k-1 (trial order).
+__global__ void k_spring_compact(const uint32_t* counts, uint32_t chunk, int d, const double* sx, const uint64_t* st,
+                                 double* ox, uint64_t* ot) {
+  __shared__ unsigned long long part[32];
+  const uint32_t k = blockIdx.x;
+  unsigned long long o = 0;
+  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) o += counts[i];
+  for (int off = 16; off > 0; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = o;
+  __syncthreads();
+  unsigned long long off = 0;
+  for (uint32_t w = 0; w < blockDim.x / 32; ++w) off += part[w];
+  const uint32_t n = counts[k];
+  const size_t src = (size_t)k * chunk;
+  for (uint32_t i = threadIdx.x; i < n * (uint32_t)d; i += blockDim.x) ox[off * d + i] = sx[src * d + i];
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) ot[off + i] = st[src + i];
+}
+
 vegas_status configure_launch(vegas_ctx* c) {
   const int d = c->cfg.ndim, N = c->cfg.nbins;
   // Histogram tile (gv::choose_tile): points per thread between gathers and
@@ -256,8 +343,9 @@ gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record) {
 }
 
 // One pass of steps 2-6 on the context stream.
-vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record) {
+vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record, bool record_max = false) {
   gv::SampleArgs A = sample_args(c, it_override);
+  if (record_max) A.cube_max = c->d_cube_max;
   void* args[] = {&A};
   CK(c, cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream));
   gv::FinArgs F = fin_args(c, refine, record);
@@ -292,7 +380,10 @@ vegas_status get_graph(vegas_ctx* c, int shape, int n1, int n2, int refine, doub
     ctl(gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, acc1);
     for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, 1, 1);
     ctl(gv::CTL_SNAPSHOT | gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, acc2);
-    for (int i = 0; i < n2 && !st; ++i) st = launch_pass(c, -1, 0, 1);
+    // the integration phase records the per-cube maxima that SPRING uses
+    if (!st && cudaMemsetAsync(c->d_cube_max, 0, sizeof(double) * c->ncubes, c->stream) != cudaSuccess)
+      st = c->fail(VEGAS_ECUDA, "cube maxima reset");
+    for (int i = 0; i < n2 && !st; ++i) st = launch_pass(c, -1, 0, 1, true);
   }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (st != VEGAS_OK) {
@@ -392,6 +483,10 @@ void vegas_destroy(vegas_ctx* c) {
   cudaFree(c->d_bins);
   cudaFree(c->d_tot);
   cudaFree(c->d_cubes);
+  cudaFree(c->d_cube_max);
+  for (void* p : {(void*)c->d_q, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
+                  (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
+    cudaFree(p);
   cudaFree(c->d_gpart);
   cudaFree(c->d_st);
   if (c->h_st) cudaFreeHost(c->h_st);
@@ -491,6 +586,7 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   if (!st) st = alloc((void**)&c->d_bins, sizeof(double) * 2 * d * N);
   if (!st) st = alloc((void**)&c->d_tot, sizeof(double) * gv::kTotCols);
   if (!st && c->strat) st = alloc((void**)&c->d_cubes, sizeof(double) * 2 * G);
+  if (!st) st = alloc((void**)&c->d_cube_max, sizeof(double) * G);
   if (!st) st = alloc((void**)&c->d_st, sizeof(GState));
   if (st) return bail(st);
   if (cudaMallocHost(&c->h_st, sizeof(GState)) != cudaSuccess)
@@ -566,6 +662,7 @@ vegas_status bases_integrate(vegas_ctx* c, int itmx1, double acc1, int itmx2, do
   if (st) return st;
   CK(c, cudaGraphLaunch(ge, c->stream));
   c->hist_upper = itmx2;
+  c->have_max = true;
   if (out || phase1) {
     if ((st = read_state(c))) return st;
     if (out) fill_result(c, out);
@@ -642,6 +739,116 @@ vegas_status vegas_get_cube_sums(vegas_ctx* c, double* sums) {
       sums[2 * i + 1] = c->h_stage[2 * i + 1] * s2;
     }
   }
+  return VEGAS_OK;
+}
+
+vegas_status vegas_get_cube_max(vegas_ctx* c, double* cmax) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (!cmax) return c->fail(VEGAS_EINVAL, "cmax is NULL");
+  if (!c->have_max) return c->fail(VEGAS_ESTATE, "no integration phase has run (bases_integrate)");
+  const size_t n = (size_t)c->ncubes;
+  vegas_status st = stage(c, n);
+  if (st) return st;
+  CK(c, cudaMemcpyAsync(c->h_stage, c->d_cube_max, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < n; ++i) cmax[i] = c->h_stage[i] * c->scale;
+  return VEGAS_OK;
+}
+
+vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, double* x_out, uint64_t* trial_out,
+                             uint32_t* n_events, uint32_t* n_overflow, uint32_t* n_nonpos) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (!n_events) return c->fail(VEGAS_EINVAL, "n_events is NULL");
+  if (!c->have_max) return c->fail(VEGAS_ESTATE, "no integration phase has run (bases_integrate)");
+  if (trial0 + (uint64_t)n_trials > 0x100000000ull) return c->fail(VEGAS_EINVAL, "trial indices must stay below 2^32");
+  if (c->ncubes > 0xFFFFFFFFull) return c->fail(VEGAS_EINVAL, "too many hypercubes");
+  *n_events = 0;
+  if (n_overflow) *n_overflow = 0;
+  if (n_nonpos) *n_nonpos = 0;
+  if (n_trials == 0) return VEGAS_OK;
+  const int d = c->cfg.ndim, N = c->cfg.nbins;
+  const uint32_t chunk = 4096, nchunks = (n_trials + chunk - 1) / chunk;
+  const bool spec = c->ke.sample == c->ke.sample_spec && c->ke.spring_spec;
+  const void* fn = spec ? c->ke.spring_spec : c->ke.spring;
+  auto grow = [&](void** p, size_t bytes) -> vegas_status {
+    cudaFree(*p);
+    *p = nullptr;
+    if (cudaMalloc(p, bytes) != cudaSuccess) return c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", bytes);
+    return VEGAS_OK;
+  };
+  vegas_status st = VEGAS_OK;
+  if (!c->d_q) {
+    if (!st) st = grow((void**)&c->d_q, sizeof(uint64_t) * c->ncubes);
+    if (!st) st = grow((void**)&c->d_prefix, sizeof(uint64_t) * (c->ncubes + 1));
+    if (!st) st = grow((void**)&c->d_meta, sizeof(double) * 3);
+    if (!st) st = grow((void**)&c->d_counters, sizeof(unsigned long long) * 2);
+  }
+  if (!st && n_trials > c->spring_cap) {
+    if (!st) st = grow((void**)&c->d_stage_x, sizeof(double) * d * (size_t)n_trials);
+    if (!st) st = grow((void**)&c->d_out_x, sizeof(double) * d * (size_t)n_trials);
+    if (!st) st = grow((void**)&c->d_stage_t, sizeof(uint64_t) * (size_t)n_trials);
+    if (!st) st = grow((void**)&c->d_out_t, sizeof(uint64_t) * (size_t)n_trials);
+    if (!st) st = grow((void**)&c->d_counts, sizeof(uint32_t) * nchunks);
+    if (!st) {
+      c->spring_cap = n_trials;
+      c->spring_chunks_cap = nchunks;
+    }
+  }
+  if (st) {
+    c->spring_cap = 0;
+    return st;
+  }
+  // integer cube table from the recorded maxima (in the integrand's units)
+  k_spring_table<<<1, 1024, 0, c->stream>>>(c->d_cube_max, (uint32_t)c->ncubes, c->scale, c->d_q, c->d_prefix,
+                                            c->d_meta);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 2, c->stream));
+  gv::SpringArgs R{};
+  R.S = sample_args(c, 0);
+  R.prefix = c->d_prefix;
+  R.q = c->d_q;
+  R.meta = c->d_meta;
+  R.out_scale = c->scale;
+  R.trial0 = (uint32_t)trial0;
+  R.n = n_trials;
+  R.chunk = chunk;
+  R.nchunks = nchunks;
+  R.stage_x = c->d_stage_x;
+  R.stage_t = c->d_stage_t;
+  R.counts = c->d_counts;
+  R.counters = c->d_counters;
+  const bool f64 = c->prec == VG_FP64;
+  const size_t smem = (size_t)d * N * (f64 ? sizeof(double2) : sizeof(float2)) +
+                      gv::kNumDerived * (f64 ? sizeof(double) : sizeof(float));
+  int occ = 0;
+  CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem));
+  if (occ < 1) return c->fail(VEGAS_EINVAL, "SPRING kernel does not fit");
+  const uint32_t blocks = std::min<uint32_t>(nchunks, (uint32_t)(c->sm_count * occ));
+  void* args[] = {&R};
+  CK(c, cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, smem, c->stream));
+  k_spring_compact<<<nchunks, 256, 0, c->stream>>>(c->d_counts, chunk, d, c->d_stage_x, c->d_stage_t, c->d_out_x,
+                                                  c->d_out_t);
+  CK(c, cudaGetLastError());
+  // status, counts and counters back to the host
+  std::vector<uint32_t> counts(nchunks);
+  double meta[3];
+  unsigned long long ctr[2];
+  CK(c, cudaMemcpyAsync(meta, c->d_meta, sizeof meta, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(counts.data(), c->d_counts, sizeof(uint32_t) * nchunks, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(ctr, c->d_counters, sizeof ctr, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (meta[2] != 0.0) return c->fail(VEGAS_ESTATE, "every recorded cube maximum is zero");
+  uint64_t total = 0;
+  for (uint32_t k : counts) total += k;
+  *n_events = (uint32_t)total;
+  if (n_overflow) *n_overflow = (uint32_t)ctr[0];
+  if (n_nonpos) *n_nonpos = (uint32_t)ctr[1];
+  if (x_out && total)
+    CK(c, cudaMemcpyAsync(x_out, c->d_out_x, sizeof(double) * d * total, cudaMemcpyDeviceToHost, c->stream));
+  if (trial_out && total)
+    CK(c, cudaMemcpyAsync(trial_out, c->d_out_t, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost, c->stream));
+  if ((x_out || trial_out) && total) CK(c, cudaStreamSynchronize(c->stream));
   return VEGAS_OK;
 }
 

@@ -229,6 +229,7 @@ struct SampleArgs {
   void* part_bins;         // [2 d N][nparts]: double, or float (hi, lo) pairs (FP32 forms)
   double* part_tot;        // [kTotCols][nparts]
   void* cubes;             // [ncubes]: double (sum w, sum w^2), or float (hi, lo, hi, lo)
+  double* cube_max;        // [ncubes] running max(0, largest w) (integration phase), or null
 };
 
 // Arguments of the reduction and finalisation kernels (steps 4-6).

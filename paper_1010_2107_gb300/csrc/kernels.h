@@ -27,6 +27,8 @@ struct KernelEntry {
   const void* grad_spec;              // k_grad<T, DM, F, 24, true> (specialised shape) or null
   int grad_nt;                        // its gradient columns (F<T, DM>::NT)
   size_t (*grad_smem)(int d, int N);
+  const void* spring;                 // k_spring<T, DM, F, YB, false>
+  const void* spring_spec;            // k_spring<T, DM, F, 24, true> or null
 };
 
 // Per-kind registries (one per random-bit width); false when no
@@ -119,6 +121,23 @@ inline int choose_lanes(uint64_t G, uint64_t nc, int threads, int64_t ctas) {
   while (L < 32 && (uint64_t)(2 * L) <= nc && G * (uint64_t)L < 4 * (uint64_t)ctas * (uint64_t)threads) L *= 2;
   return L;
 }
+
+// Arguments of the SPRING trial kernel: trials trial0 .. trial0 + n - 1 in
+// chunks of `chunk` trials; the kept points of chunk k go, in trial order, to
+// stage_x[(k chunk + i) d + a] and stage_t[k chunk + i], their number to
+// counts[k]; counters: [0] bound overflows, [1] non-positive weights.
+struct SpringArgs {
+  SampleArgs S;
+  const uint64_t* prefix;   // [G + 1] exclusive prefix sums of the integer cube weights
+  const uint64_t* q;        // [G] integer cube weights
+  const double* meta;       // {Q, scale} written by the table kernel
+  double out_scale;         // integrand output scale: weights in the integrand's units
+  uint32_t trial0, n, chunk, nchunks;
+  double* stage_x;
+  uint64_t* stage_t;
+  uint32_t* counts;
+  unsigned long long* counters;
+};
 
 // Arguments of the per-sample dump kernel.
 struct DumpArgs {

@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
   fpair tp[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (!A.strat) {
     Run<ACC> sw, sw2;
+    H pmax = H(0);  // largest weight (integration-phase maximum of the one cube)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t first = (uint64_t)blockIdx.x * blockDim.x;
     const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
@@ -433,11 +434,13 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
         if (v0) {
           sw.add(w0);
           sw2.add(w0 * w0);
+          pmax = max(pmax, w0);
           scatter(kb0, w0);
         }
         if (v1) {
           sw.add(w1);
           sw2.add(w1 * w1);
+          pmax = max(pmax, w1);
           scatter(kb1, w1);
         }
         if ((pend += 2) >= A.ppt) {
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
           const H w = eval_point((uint32_t)s, kb);
           sw.add(w);
           sw2.add(w * w);
+          pmax = max(pmax, w);
           scatter(kb, w);
         }
         if (++pend == A.ppt) {
@@ -461,6 +465,13 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
       }
     }
     if (pend) gather();
+    if (A.cube_max) {  // non-negative doubles order as their bit patterns
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off));
+      if (lane == 0 && pmax > H(0))
+        atomicMax(reinterpret_cast<unsigned long long*>(A.cube_max),
+                  (unsigned long long)__double_as_longlong((double)pmax));
+    }
     if constexpr (COMP) {
       tp[0] = sw.p;
       tp[1] = sw2.p;
@@ -504,8 +515,9 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
       }
       const uint32_t s0 = c * A.nc;
       // a lane's chain of points in one cube is short: plain sums in H,
-      // compensated merges across the group
-      H p1 = H(0), p2 = H(0);
+      // compensated merges across the group; pmax: the largest weight (for
+      // the per-cube maxima of the integration phase)
+      H p1 = H(0), p2 = H(0), pmax = H(0);
       if constexpr (PAIR) {
         for (uint32_t i = 0; i < per_lane; i += 2) {
           const uint32_t j0 = gl + i * Lw, j1 = j0 + Lw;
@@ -516,11 +528,13 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
           if (v0) {
             p1 += w0;
             p2 += w0 * w0;
+            pmax = max(pmax, w0);
             scatter(kb0, w0);
           }
           if (v1) {
             p1 += w1;
             p2 += w1 * w1;
+            pmax = max(pmax, w1);
             scatter(kb1, w1);
           }
           if ((pend += 2) >= A.ppt) {
@@ -536,6 +550,7 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
             const H w = eval_point(s0 + j, kb);
             p1 += w;
             p2 += w * w;
+            pmax = max(pmax, w);
             scatter(kb, w);
           }
           if (++pend == A.ppt) {
@@ -543,6 +558,10 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
             pend = 0;
           }
         }
+      }
+      if (A.cube_max) {  // integration phase: per-cube maxima (one group per cube)
+        for (int off = Lw >> 1; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off, Lw));
+        if (live && gl == 0) A.cube_max[c] = fmax(A.cube_max[c], (double)pmax);
       }
       if constexpr (COMP) {
         fpair c1{p1, 0.f}, c2{p2, 0.f};
@@ -652,6 +671,129 @@ inline size_t sample_smem_bytes(int d, int N, int cap) {
 
 // Steps 2-3 for a list of sample indices (parity checks and debugging):
 // the Philox words, bins, point, Jacobian and integrand value of each.
+// SPRING trials (event generation on the frozen grid of the BASES
+// integration phase; the reading is that of the oracle): trial t draws
+// Philox words from counter (t, word group, 0xFFFFFFFF, instance); words
+// 0..W-1 place the point as the sampling step does, words W and W+1 pick
+// the cube through the integer prefix sums, the next word (two for 53-bit
+// words) gives v, and the trial is kept iff w > 0 and (w exceeds the cube's
+// bound, or v times the bound is below w), the comparison in FP64.  Each
+// chunk of trials is compacted in trial order (warp ballots, then warps in
+// order).  One thread per trial and round; 256 threads.
+constexpr uint32_t kSpringIt = 0xFFFFFFFFu;
+
+template <typename T, int DM, template <typename, int> class F, int YB, bool SPEC>
+__global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
+  using T2 = typename Vec2<T>::type;
+  const SampleArgs& A = R.S;
+  const int d = SPEC ? DM : A.d, N = A.N, dN = d * N;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T2* tab = reinterpret_cast<T2*>(smem);
+  T* P = reinterpret_cast<T*>(smem + (size_t)dN * sizeof(T2));
+  __shared__ uint32_t wcount[8];
+  __shared__ uint32_t chunk_count;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T2* gtab = reinterpret_cast<const T2*>(A.tab);
+  for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
+  for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
+  __syncthreads();
+  const double Q = R.meta[0], scale = R.meta[1];
+  const uint64_t Qi = (uint64_t)Q;
+  const uint32_t G = A.ncubes;
+  const int W = YB == 24 ? d : 2 * d;
+  unsigned long long ov = 0, np = 0;
+  for (uint32_t chunk = blockIdx.x; chunk < R.nchunks; chunk += gridDim.x) {
+    if (tid == 0) chunk_count = 0;
+    const uint32_t base = chunk * R.chunk;
+    for (uint32_t r = 0; r < R.chunk; r += blockDim.x) {
+      const uint32_t rel = base + r + tid;
+      bool keep = false;
+      T x[DM];
+      if (rel < R.n) {
+        const uint32_t t = R.trial0 + rel;
+        // words W .. W+3 (cube and acceptance): at most two Philox blocks
+        uint32_t wx[8];
+        const int g0 = W >> 2;
+        const uint4 b0 = philox4x32_10(make_uint4(t, (uint32_t)g0, kSpringIt, A.instance), A.ks);
+        const uint4 b1 = philox4x32_10(make_uint4(t, (uint32_t)(g0 + 1), kSpringIt, A.instance), A.ks);
+        wx[0] = b0.x; wx[1] = b0.y; wx[2] = b0.z; wx[3] = b0.w;
+        wx[4] = b1.x; wx[5] = b1.y; wx[6] = b1.z; wx[7] = b1.w;
+        const int o = W & 3;
+        const uint64_t U = ((uint64_t)wx[o] << 32) | (uint64_t)wx[o + 1];
+        const uint64_t u = __umul64hi(U, Qi);
+        uint32_t lo = 0, hi = G;  // prefix[lo] <= u < prefix[hi]
+        while (hi - lo > 1) {
+          const uint32_t mid = lo + ((hi - lo) >> 1);
+          if (__ldg(R.prefix + mid) <= u)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        const uint32_t c = lo;
+        int cd[DM];
+        uint32_t rest = c;
+#pragma unroll
+        for (int a = 0; a < DM; ++a) {
+          cd[a] = 0;
+          if (a < d) {
+            if (A.g_pow2) {
+              cd[a] = (int)(rest & (uint32_t)(A.g - 1));
+              rest >>= A.g_log2;
+            } else {
+              cd[a] = (int)(rest % (uint32_t)A.g);
+              rest /= (uint32_t)A.g;
+            }
+          }
+        }
+        int kb[DM];  // bins: not needed here
+        const T J = make_point<T, DM, YB, SPEC>(A, kSpringIt, t, cd, tab, x, kb, nullptr);
+        const double w = (double)(F<T, DM>::eval(x, d, P) * J) * R.out_scale;
+        const double v = YB == 24 ? (double)(wx[o + 2] >> 8) * (1.0 / 16777216.0)
+                                  : ((double)(wx[o + 2] >> 5) * 67108864.0 + (double)(wx[o + 3] >> 6)) *
+                                        (1.0 / 9007199254740992.0);
+        const double Mt = (double)__ldg(R.q + c) / scale;
+        if (!(w > 0.0)) {
+          ++np;
+        } else if (w > Mt) {
+          ++ov;
+          keep = true;
+        } else {
+          keep = v * Mt < w;
+        }
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      uint32_t off = chunk_count, tot = 0;
+      for (int k = 0; k < nw; ++k) {
+        if (k < warp) off += wcount[k];
+        tot += wcount[k];
+      }
+      if (keep) {
+        const uint32_t pos = base + off + __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+        for (int a = 0; a < DM; ++a)
+          if (a < d) R.stage_x[(size_t)pos * d + a] = (double)x[a];
+        R.stage_t[pos] = (uint64_t)R.trial0 + rel;
+      }
+      __syncthreads();
+      if (tid == 0) chunk_count += tot;
+      __syncthreads();
+    }
+    if (tid == 0) R.counts[chunk] = chunk_count;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ov += __shfl_xor_sync(0xffffffffu, ov, off);
+    np += __shfl_xor_sync(0xffffffffu, np, off);
+  }
+  if (lane == 0) {
+    if (ov) atomicAdd(R.counters, ov);
+    if (np) atomicAdd(R.counters + 1, np);
+  }
+}
+
 template <typename T, int DM, template <typename, int> class F, int YB>
 __global__ void __launch_bounds__(256) k_dump(const DumpArgs D) {
   __shared__ __align__(16) T P[kNumDerived];  // paired loads read 8-byte pairs
@@ -832,6 +974,11 @@ inline KernelEntry make_entry() {
   e.sample_spec = spec_kernel<T, DM, F, ACC, YB>();
   grad_entry<T, DM, F, YB>(e);
   e.dump = (const void*)&k_dump<T, DM, F, YB>;
+  e.spring = (const void*)&k_spring<T, DM, F, YB, false>;
+  if constexpr (YB == 24)
+    e.spring_spec = (const void*)&k_spring<T, DM, F, 24, true>;
+  else
+    e.spring_spec = nullptr;
   e.smem = &sample_smem_bytes<T, ACC>;
   e.dm = DM;
   e.spec_ppt_min = kPairPoints<T, DM, true> ? 2 : 1;

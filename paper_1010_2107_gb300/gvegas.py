@@ -85,6 +85,10 @@ _SIGS = {
     "vegas_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vegas_get_cube_max": (ctypes.c_int, [_P, _DP]),
+    "spring_generate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _DP,
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "vegas_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
     "vegas_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
@@ -297,6 +301,28 @@ def vegas_get_launch(ctx: Context):
     t, c, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().vegas_get_launch(ctx.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(o)), ctx.handle)
     return dict(threads=t.value, ctas=c.value, occupancy=o.value)
+
+
+def vegas_get_cube_max(ctx: Context):
+    """Per-hypercube maxima of the last integration phase (SPRING bounds)."""
+    g = max(ctx.nstrat, 1)
+    out = np.zeros(g ** ctx.ndim)
+    _check(lib().vegas_get_cube_max(ctx.handle, _dp(out)), ctx.handle)
+    return out
+
+
+def spring_generate(ctx: Context, trial0: int, n_trials: int, events: bool = True):
+    """SPRING trials trial0 .. trial0 + n_trials - 1; returns the kept points
+    (host copies when `events`), their trial indices, and the counts."""
+    n_ev, n_ov, n_np = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    x = np.zeros((n_trials, ctx.ndim)) if events else None
+    t = np.zeros(n_trials, dtype=np.uint64) if events else None
+    _check(lib().spring_generate(ctx.handle, int(trial0), int(n_trials), _dp(x) if events else None,
+                                 t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if events else None,
+                                 ctypes.byref(n_ev), ctypes.byref(n_ov), ctypes.byref(n_np)), ctx.handle)
+    k = n_ev.value
+    return dict(x=x[:k] if events else None, trial=t[:k] if events else None, n_events=k,
+                overflow=n_ov.value, nonpos=n_np.value)
 
 
 def vegas_set_tile(ctx: Context, points_per_thread: int = 0):
