@@ -45,6 +45,11 @@ ALGO_OPS = {
                    accumulate=20 * 2 + 14),
     "rambo4_adjoint": dict(philox=4 * 10 * 6, bins=16 * 6, map=16 * 3,
                            integrand=4 * 60 + 6 * 8 + 4 * 14 + 10 + 4 * 6 + 20, accumulate=5 * 7),
+    # per SPRING trial: three Philox blocks (8 point words, 2 cube words,
+    # 1 acceptance word), a 16-step bisection over the cube table, bins,
+    # map, integrand and the keep decision
+    "spring_dgauss8": dict(philox=3 * 10 * 6, cube_search=16 * 3, bins=8 * 6, map=8 * 3,
+                           integrand=8 * 4 + 8, keep=10),
 }
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/); None until captured for the current kernel.
@@ -170,6 +175,22 @@ def oracle_rate(name: str, iters_refine: int, iters_frozen: int):
     return n / dt, n, dt
 
 
+def oracle_spring_rate(R, h, n=1 << 20):
+    """The oracle's SPRING on the context's own grid and cube maxima."""
+    import oracle
+    oracle.build()
+    gv, w = R.gv, R.w
+    d = w["ndim"]
+    cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
+                          seed=w["seed"])
+    fn = oracle.Integrand(w["kind"], d, w["params"])
+    edges, cmax = gv.vegas_get_grid(h), gv.vegas_get_cube_max(h)
+    t = time.perf_counter()
+    oracle.spring(cfg, fn, edges, cmax, 0, n)
+    dt = time.perf_counter() - t
+    return n / dt, n, dt
+
+
 def _oracle_worker(job):
     """One process of the all-core CPU baseline: the oracle on its own
     instance word (a disjoint Philox counter range), timed inside."""
@@ -204,6 +225,51 @@ def oracle_rate_allcores(name: str):
     return n / dt, n, dt, P
 
 
+def _reference_step(name):
+    """One step of the reference arm (the oracle as it stands): returns a
+    callable giving (points, seconds, description of the sample)."""
+    import oracle
+    if name == "genz256":
+        from paper_1010_2107_gb300 import workloads as wl
+        insts = wl.genz_batch(wl.GENZ256["count"], wl.GENZ256["seed"])
+        chosen, tot = [], 0
+        for ins in insts:  # the leading instances, about 2^22 points in all
+            chosen.append(ins)
+            tot += ins["ncall"]
+            if tot >= 1 << 22:
+                break
+
+        def step():
+            t = time.perf_counter()
+            for ins in chosen:
+                cfg = oracle.make_cfg(ins["ndim"], nbins=wl.GENZ256["nbins"], ncall=ins["ncall"], ybits=24,
+                                      seed=wl.GENZ256["sample_seed"], instance=ins["instance"])
+                fn = oracle.Integrand(ins["kind"], ins["ndim"], ins["params"])
+                oracle.iteration(cfg, fn, oracle.uniform_grid(ins["ndim"], wl.GENZ256["nbins"]), 0)
+            return tot, time.perf_counter() - t, f"one iteration of the first {len(chosen)} instances ({tot} points)"
+        return step
+    w = _workload(name)
+    if w.get("mode") == "spring":
+        d = w["ndim"]
+        cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
+                              seed=w["seed"])
+        fn = oracle.Integrand(w["kind"], d, w["params"])
+        e = oracle.uniform_grid(d, w["nbins"])
+        cmax = oracle.iteration(cfg, fn, e, 0, cubes=True)["Cmax"]  # bounds from one iteration
+        n = 1 << 20
+
+        def step():
+            t = time.perf_counter()
+            oracle.spring(cfg, fn, e, cmax, 0, n)
+            return n, time.perf_counter() - t, f"{n} SPRING trials on the uniform grid"
+        return step
+
+    def step():
+        _, n, dt = oracle_rate(name, 1, 0)
+        return n, dt, f"one grid-optimising iteration of NCALL={w['ncall']}"
+    return step
+
+
 def run_reference(args):
     rank, world, _, dist = _dist()
     if rank != 0:
@@ -211,23 +277,23 @@ def run_reference(args):
     import oracle
     oracle.build()
     name = args.workload
-    w = _workload(name)
+    step = _reference_step(name)
     for _ in range(args.warmup):
-        oracle_rate(name, 1, 0)
-    times = []
+        step()
+    times, npts = [], 0
     for _ in range(args.steps):
-        _, n, dt = oracle_rate(name, 1, 0)
+        n, dt, sample = step()
         times.append(dt)
+        npts += n
     total = sum(times)
-    value = args.steps * w["ncall"] / total
+    value = npts / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(name),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one grid-optimising iteration of NCALL={w['ncall']} per step, "
-                                   "single-threaded FP64 C oracle"},
+                         "sample": f"{sample} per step, single-threaded FP64 C oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -247,7 +313,10 @@ def _config(name):
          "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw"}[w["kind"]],
          "precision": w["precision"], "ybits": w["ybits"], "nstrat": w["nstrat"],
          "l2": "flushed between steps (512 MiB write)"}
-    if w.get("mode") == "bases":
+    if w.get("mode") == "spring":
+        c["iterations"] = (f"{w['ntrials']} SPRING trials per step on the frozen grid of a "
+                           f"{w['itmx1']}+{w['itmx2']} BASES run")
+    elif w.get("mode") == "bases":
         c["iterations"] = f"{w['itmx1']}+{w['itmx2']} (BASES)"
     elif w.get("mode") == "adjoint":
         c["iterations"] = f"one gradient pass on the grid of {w['warmup_iters']} refining iterations"
@@ -307,6 +376,10 @@ class Runner:
                             precision=prec, ybits=w["ybits"], stream=self.stream)
         if self.mode == "adjoint":  # the grid the gradient is taken on
             gv.vegas_iterate(h, w["warmup_iters"], refine=True)
+        elif self.mode == "spring":  # the BASES run whose integration phase bounds the cubes
+            tuned = gv.vegas_autotune(h)
+            self.tuned = self.tuned or tuned
+            gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
         else:
             tuned = gv.vegas_autotune(h)
             self.tuned = self.tuned or tuned
@@ -321,6 +394,8 @@ class Runner:
             return w["ncall"] * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return w["ncall"]
+        if self.mode == "spring":
+            return w["ntrials"]
         return w["ncall"] * w["itmx"]
 
     @property
@@ -336,6 +411,8 @@ class Runner:
             return 2 + 2 + 2 * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return 2
+        if self.mode == "spring":  # cube table, trials, compaction
+            return 3
         return 2 + 2 + 2 * w["itmx"]
 
     def step(self, h):
@@ -348,6 +425,8 @@ class Runner:
             gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
         elif self.mode == "adjoint":
             gv.vegas_grad(h, 1000)
+        elif self.mode == "spring":
+            gv.spring_generate(h, 0, w["ntrials"], events=False)
         else:
             gv.vegas_reset_grid(h)
             gv.vegas_reset_results(h)
@@ -362,6 +441,10 @@ class Runner:
         if self.mode == "adjoint":
             g, I = gv.vegas_grad(h, 1000)
             return {"I": I, "dI_dM": g[0], "dI_dGamma": g[1], "dI_dT": g[2]}
+        if self.mode == "spring":
+            r = gv.spring_generate(h, 0, self.w["ntrials"], events=False)
+            return {"events": r["n_events"], "acceptance": r["n_events"] / self.w["ntrials"],
+                    "overflow": r["overflow"], "nonpos": r["nonpos"]}
         r = gv.vegas_iterate(h, 0, refine=False)
         return {"I": r["I"], "sigma": r["sigma"], "chi2_dof": r["chi2_dof"], "nonfinite": r["nonfinite"]}
 
@@ -383,6 +466,8 @@ class Runner:
             b.record(self.stream)
             torch.cuda.synchronize()
             return "k_grad", a.elapsed_time(b) / 5, self.w["ncall"], {}
+        if self.mode == "spring":
+            return "k_spring", gv.spring_profile(h, self.w["ntrials"], 5), self.w["ntrials"], {}
         p = gv.vegas_profile_pass(h, 20)
         return "k_sample", p["sample"], self.w["ncall"], {"finish_ms": p["finish"]}
 
@@ -410,6 +495,9 @@ class Runner:
             gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=True)
             return 0, 48 * len(self.insts) + 1200 * len(self.insts)
         d, N = w["ndim"], w["nbins"]
+        if self.mode == "spring":  # events copied to host memory; the frozen grid stays
+            r = gv.spring_generate(h, 0, w["ntrials"], events=True)
+            return 0, r["n_events"] * (8 * d + 8)
         edges0 = np.tile(np.arange(N + 1, dtype=np.float64) / N, (d, 1))
         gv.vegas_set_grid(h, edges0)
         gv.vegas_set_params(h, np.asarray(w["params"], dtype=np.float64))
@@ -525,6 +613,11 @@ def run_ours(args):
            "d2h_bytes_per_step": d2h, "steps": ke}
 
     cpu = cpu_all = None
+    if rank == 0 and world == 1 and not args.no_cpu and R.mode == "spring":
+        rate, n, dt = oracle_spring_rate(R, h)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} SPRING trials on the same frozen grid and cube maxima, {dt:.1f} s "
+                         "single-threaded FP64 C oracle"}
     if rank == 0 and world == 1 and not args.no_cpu and R.mode in ("bases", "vegas"):
         bases = R.mode == "bases"
         rate, n, dt = oracle_rate(args.workload, 3, 3) if bases else oracle_rate(args.workload, 1, 0)
@@ -594,7 +687,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dgauss8",
-                    choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256"])
+                    choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256", "spring_dgauss8"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

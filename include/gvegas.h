@@ -248,6 +248,10 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
  * *n_events = k.  VEGAS_ESTATE before any bases_integrate or when every
  * maximum is zero; EINVAL when trial0 + n_trials exceeds 2^32. */
 vegas_status vegas_get_cube_max(vegas_ctx* ctx, double* cmax);
+/* Measurement: mean milliseconds of the SPRING trial kernel alone (CUDA
+ * events on the context stream around it) over `reps` spring_generate calls
+ * of n_trials trials from trial 0, events left on the device. */
+vegas_status spring_profile(vegas_ctx* ctx, uint32_t n_trials, int reps, double* ms);
 vegas_status spring_generate(vegas_ctx* ctx, uint64_t trial0, uint32_t n_trials,
                              double* x_out, uint64_t* trial_out, uint32_t* n_events,
                              uint32_t* n_overflow, uint32_t* n_nonpos);

@@ -76,6 +76,7 @@ struct vegas_ctx {
   uint32_t* d_counts = nullptr;
   unsigned long long* d_counters = nullptr;
   uint32_t spring_cap = 0, spring_chunks_cap = 0;
+  cudaEvent_t spring_timer[2] = {nullptr, nullptr};  // set by spring_profile around the trial kernel
   double* d_gpart = nullptr;  // adjoint partials [grad_nt + 2][grad_ctas] then totals
   int grad_ctas = 0;
   size_t grad_smem = 0;
@@ -826,7 +827,9 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   if (occ < 1) return c->fail(VEGAS_EINVAL, "SPRING kernel does not fit");
   const uint32_t blocks = std::min<uint32_t>(nchunks, (uint32_t)(c->sm_count * occ));
   void* args[] = {&R};
+  if (c->spring_timer[0]) CK(c, cudaEventRecord(c->spring_timer[0], c->stream));
   CK(c, cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, smem, c->stream));
+  if (c->spring_timer[1]) CK(c, cudaEventRecord(c->spring_timer[1], c->stream));
   k_spring_compact<<<nchunks, 256, 0, c->stream>>>(c->d_counts, chunk, d, c->d_stage_x, c->d_stage_t, c->d_out_x,
                                                   c->d_out_t);
   CK(c, cudaGetLastError());
@@ -849,6 +852,32 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   if (trial_out && total)
     CK(c, cudaMemcpyAsync(trial_out, c->d_out_t, sizeof(uint64_t) * total, cudaMemcpyDeviceToHost, c->stream));
   if ((x_out || trial_out) && total) CK(c, cudaStreamSynchronize(c->stream));
+  return VEGAS_OK;
+}
+
+vegas_status spring_profile(vegas_ctx* c, uint32_t n_trials, int reps, double* ms) {
+  if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
+  if (reps < 1 || !ms) return c->fail(VEGAS_EINVAL, "need reps >= 1 and ms");
+  uint32_t k = 0;
+  vegas_status st = spring_generate(c, 0, n_trials, nullptr, nullptr, &k, nullptr, nullptr);  // buffers, warm-up
+  if (st) return st;
+  cudaEvent_t a, b;
+  CK(c, cudaEventCreate(&a));
+  CK(c, cudaEventCreate(&b));
+  double acc = 0.0;
+  for (int r = 0; r < reps && !st; ++r) {
+    c->spring_timer[0] = a;
+    c->spring_timer[1] = b;
+    st = spring_generate(c, 0, n_trials, nullptr, nullptr, &k, nullptr, nullptr);
+    float t = 0.f;
+    if (!st && cudaEventElapsedTime(&t, a, b) != cudaSuccess) st = c->fail(VEGAS_ECUDA, "event timing");
+    acc += t;
+  }
+  c->spring_timer[0] = c->spring_timer[1] = nullptr;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st) return st;
+  *ms = acc / reps;
   return VEGAS_OK;
 }
 

@@ -86,6 +86,7 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "vegas_get_cube_max": (ctypes.c_int, [_P, _DP]),
+    "spring_profile": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_int, _DP]),
     "spring_generate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32, _DP,
                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32),
                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
@@ -323,6 +324,13 @@ def spring_generate(ctx: Context, trial0: int, n_trials: int, events: bool = Tru
     k = n_ev.value
     return dict(x=x[:k] if events else None, trial=t[:k] if events else None, n_events=k,
                 overflow=n_ov.value, nonpos=n_np.value)
+
+
+def spring_profile(ctx: Context, n_trials: int, reps: int = 5):
+    """Mean ms of the SPRING trial kernel over `reps` calls of n_trials."""
+    ms = ctypes.c_double()
+    _check(lib().spring_profile(ctx.handle, int(n_trials), int(reps), ctypes.byref(ms)), ctx.handle)
+    return ms.value
 
 
 def vegas_set_tile(ctx: Context, points_per_thread: int = 0):

@@ -81,6 +81,10 @@ WORKLOADS = {
     "rambo4_adjoint": dict(kind=RAMBO_BW, ndim=16, params=rambo_params(4, cut=1),
                            nbins=50, ncall=1 << 24, warmup_iters=5, nstrat=0,
                            seed=1, precision="fp32", ybits=24, mode="adjoint"),
+    # SPRING on the dgauss8 BASES run: 2^24 trials per step on its frozen grid
+    "spring_dgauss8": dict(kind=DOUBLE_GAUSSIAN, ndim=8, params=double_gaussian_params(),
+                           nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,
+                           precision="fp32", ybits=24, mode="spring", ntrials=1 << 24),
 }
 
 
