@@ -36,8 +36,9 @@ METRIC = "samples/sec per VEGAS/BASES iteration vs plain FP64 GPU path; % FP32 p
 UNIT = "samples/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Algorithmic FP32-pipe operations per point of the sampling kernel (see
-# DESIGN.md, "Roofline"): Philox, word->bin/position, map, integrand, sums.
+# Algorithmic FP32-pipe operations per point of the sampling kernel:
+# Philox, word->bin/position, map, integrand, sums (the roofline's unit of
+# work; the peak is the FP32 issue rate of all SMs at the maximum clock).
 ALGO_OPS = {
     "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, accumulate=8 * 2 + 2 + 12),
     "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),

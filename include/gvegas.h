@@ -231,7 +231,7 @@ vegas_status vegas_sample_dump(vegas_ctx* ctx, uint32_t it, const uint64_t* s,
                                double* x, double* jac, double* f);
 
 /* SPRING (Sec. 2.1: the results of the BASES integration phase drive event
- * generation; the steps are Kawabata's SPRING as this build reads them).
+ * generation; the steps follow Kawabata's SPRING, with integer cube choice).
  * Every bases_integrate records, during its integration phase, the largest
  * weight M_c = max(0, f J) seen in each hypercube c.
  * vegas_get_cube_max copies those maxima (in the integrand's units, like

@@ -162,8 +162,8 @@ int orc_bases(const orc_cfg* cfg, const orc_fn* fn, double* edges,
               double* hist, double out[3], int n_done[2]);
 
 /* SPRING (unweighted events from the BASES integration phase; Sec. 2.1
- * names it, Kawabata's BASES/SPRING defines it; the steps below are this
- * build's reading).  orc_spring_table: integer hypercube weights
+ * names it, Kawabata's BASES/SPRING defines it; the steps below follow it,
+ * with an integer cube choice).  orc_spring_table: integer hypercube weights
  * q_c = ceil(M_c * scale), scale = 2^24 / max_c M_c, from the per-cube
  * maxima M_c; returns -1 when every M_c is 0.  orc_spring: trials
  * t = t0 .. t0 + n - 1, each from the Philox words of counter

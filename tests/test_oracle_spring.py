@@ -1,6 +1,6 @@
 """Pins of the oracle's SPRING (event generation on the frozen grid of the
-BASES integration phase; Sec. 2.1 names it, the steps are this build's
-reading) against what the mathematics fixes:
+BASES integration phase; Sec. 2.1 names it, the steps follow Kawabata's
+SPRING with an integer cube choice) against what the mathematics fixes:
 
 * the integer cube table is the stated ceiling, recomputed in numpy;
 * per-cube maxima are the brute-force maxima of the weights;
