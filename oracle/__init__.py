@@ -31,6 +31,8 @@ GENZ_CORNER_PEAK = 2
 GENZ_OSCILLATORY = 3
 DOUBLE_GAUSSIAN = 4
 RAMBO_BW = 5
+GENZ_CONTINUOUS = 6
+GENZ_DISCONTINUOUS = 7
 
 _lock = threading.Lock()
 _lib = None

@@ -352,6 +352,8 @@ static int fn_valid(const orc_fn* fn) {
     case ORC_GENZ_CORNER_PEAK: return fn->nparams >= d;
     case ORC_GENZ_OSCILLATORY: return fn->nparams >= d + 1;
     case ORC_DOUBLE_GAUSSIAN: return fn->nparams >= 3;
+    case ORC_GENZ_CONTINUOUS: return fn->nparams >= 2 * d;
+    case ORC_GENZ_DISCONTINUOUS: return fn->nparams >= d + (d < 2 ? d : 2);
     case ORC_RAMBO_BW: {
       if (fn->nparams < ORC_RB_NPARAMS) return 0;
       int n = (int)fn->params[ORC_RB_N];
@@ -392,6 +394,22 @@ static double eval_point(const orc_fn* fn, const double* x, double* grad) {
       double t = 1.0;
       for (int i = 0; i < d; ++i) t += P[i] * x[i];
       return pow(t, -(double)(d + 1));
+    }
+    case ORC_GENZ_CONTINUOUS: {
+      /* f = exp(-sum_i a_i |x_i - u_i|)  (Genz 1984, "continuous") */
+      const double *a = P, *u = P + d;
+      double q = 0.0;
+      for (int i = 0; i < d; ++i) q += a[i] * fabs(x[i] - u[i]);
+      return exp(-q);
+    }
+    case ORC_GENZ_DISCONTINUOUS: {
+      /* f = exp(sum_i a_i x_i) if x_1 <= u_1 and x_2 <= u_2, else 0
+       * (Genz 1984, "discontinuous"; only x_1 for d = 1) */
+      const double *a = P, *u = P + d;
+      if (x[0] > u[0] || (d > 1 && x[1] > u[1])) return 0.0;
+      double t = 0.0;
+      for (int i = 0; i < d; ++i) t += a[i] * x[i];
+      return exp(t);
     }
     case ORC_GENZ_OSCILLATORY: {
       /* f = cos(2 pi u_1 + sum_i a_i x_i) */

@@ -40,7 +40,9 @@ enum {
   ORC_GENZ_CORNER_PEAK = 2,  /* params: a[d]                                */
   ORC_GENZ_OSCILLATORY = 3,  /* params: a[d], u1                            */
   ORC_DOUBLE_GAUSSIAN = 4,   /* params: c1, c2, w                           */
-  ORC_RAMBO_BW = 5           /* params: see ORC_RB_* below, d = 4 n         */
+  ORC_RAMBO_BW = 5,          /* params: see ORC_RB_* below, d = 4 n         */
+  ORC_GENZ_CONTINUOUS = 6,   /* params: a[d], u[d]                          */
+  ORC_GENZ_DISCONTINUOUS = 7 /* params: a[d], u[min(d, 2)]                  */
 };
 
 /* RAMBO + Breit-Wigner parameter slots. */

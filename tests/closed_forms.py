@@ -48,6 +48,44 @@ def genz_oscillatory(a, u1):
     return z.real
 
 
+def genz_continuous(a, u):
+    """int exp(-sum a_i |x_i - u_i|) dx = prod_i (2 - e^{-a_i u_i} - e^{-a_i (1 - u_i)}) / a_i."""
+    return math.prod((2 - math.exp(-ai * ui) - math.exp(-ai * (1 - ui))) / ai for ai, ui in zip(a, u))
+
+
+def genz_discontinuous(a, u):
+    """int_{x_1 <= u_1, x_2 <= u_2} exp(sum a_i x_i) dx
+       = prod_{i < min(d,2)} (e^{a_i u_i} - 1)/a_i * prod_{i >= 2} (e^{a_i} - 1)/a_i."""
+    out = 1.0
+    for i, ai in enumerate(a):
+        top = u[i] if i < 2 else 1.0
+        out *= math.expm1(ai * top) / ai
+    return out
+
+
+def gauss_legendre_split(breaks, nodes_per_piece=16, pieces=8):
+    """1-D composite Gauss-Legendre rule on [0, 1] whose pieces never straddle
+    a point of `breaks` (kinks and jumps of the integrand sit on piece ends)."""
+    xg, wg = np.polynomial.legendre.leggauss(nodes_per_piece)
+    pts = sorted({0.0, 1.0, *[b for b in breaks if 0.0 < b < 1.0]})
+    xs, ws = [], []
+    for lo, hi in zip(pts[:-1], pts[1:]):
+        edges = np.linspace(lo, hi, pieces + 1)
+        for a, b in zip(edges[:-1], edges[1:]):
+            xs.append(a + (b - a) * 0.5 * (xg + 1))
+            ws.append(0.5 * (b - a) * wg)
+    return np.concatenate(xs), np.concatenate(ws)
+
+
+def tensor_rule(rules):
+    """Tensor product of 1-D rules [(x, w), ...]: nodes [n][d] and weights [n]."""
+    grids = np.meshgrid(*[r[0] for r in rules], indexing="ij")
+    wgrids = np.meshgrid(*[r[1] for r in rules], indexing="ij")
+    X = np.stack([g.ravel() for g in grids], axis=1)
+    W = np.prod(np.stack([g.ravel() for g in wgrids], axis=1), axis=1)
+    return X, W
+
+
 def double_gaussian(c1, c2, w, d):
     """int 1/2 sum_c (w sqrt pi)^-d exp(-sum ((x_i-c)/w)^2) dx
        = 1/2 sum_c prod_i 1/2 [erf((1-c)/w) + erf(c/w)]."""

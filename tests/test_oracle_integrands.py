@@ -71,6 +71,47 @@ def test_genz_oscillatory_quadrature(orc, d):
     assert abs(got - cf.genz_oscillatory(a, u1)) < 1e-12
 
 
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_genz_continuous_quadrature(orc, d):
+    """Kinks at u_i: a rule whose pieces end there integrates each smooth
+    piece to rounding, against the closed form."""
+    rng = np.random.default_rng(40 + d)
+    a = rng.uniform(1, 8, d)
+    u = rng.uniform(0.1, 0.9, d)
+    fn = orc.Integrand(orc.GENZ_CONTINUOUS, d, np.concatenate([a, u]))
+    n = 16 if d < 3 else 8
+    X, W = cf.tensor_rule([cf.gauss_legendre_split([u[i]], n, 4) for i in range(d)])
+    assert float(np.sum(W * orc.integrand(fn, X))) == pytest.approx(cf.genz_continuous(a, u), rel=1e-12)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_genz_discontinuous_quadrature(orc, d):
+    """Jumps at u_1 (and u_2): rules with pieces ending there; the integrand
+    is zero beyond them and exp(sum a_i x_i) before."""
+    rng = np.random.default_rng(50 + d)
+    a = rng.uniform(0.5, 4, d)
+    u = rng.uniform(0.2, 0.8, min(d, 2))
+    fn = orc.Integrand(orc.GENZ_DISCONTINUOUS, d, np.concatenate([a, u]))
+    n = 16 if d < 3 else 8
+    X, W = cf.tensor_rule([cf.gauss_legendre_split([u[i]] if i < 2 else [], n, 4) for i in range(d)])
+    assert float(np.sum(W * orc.integrand(fn, X))) == pytest.approx(cf.genz_discontinuous(a, u), rel=1e-12)
+
+
+def test_genz_discontinuous_edges_and_separability(orc):
+    a, u = np.array([1.5, 2.0, 0.7]), np.array([0.4, 0.6])
+    fn = orc.Integrand(orc.GENZ_DISCONTINUOUS, 3, np.concatenate([a, u]))
+    x = np.array([[0.4, 0.6, 0.3], [0.4000001, 0.1, 0.1], [0.1, 0.6000001, 0.9], [0.1, 0.2, 0.99]])
+    f = orc.integrand(fn, x)
+    assert f[0] == pytest.approx(math.exp(a @ x[0]), rel=1e-15)  # the boundary point belongs to the region
+    assert f[1] == 0.0 and f[2] == 0.0
+    assert f[3] == pytest.approx(math.exp(a @ x[3]), rel=1e-15)
+    fc = orc.Integrand(orc.GENZ_CONTINUOUS, 3, np.concatenate([a, [0.3, 0.5, 0.7]]))
+    X = np.random.default_rng(0).random((200, 3))
+    one = [orc.Integrand(orc.GENZ_CONTINUOUS, 1, [a[i], [0.3, 0.5, 0.7][i]]) for i in range(3)]
+    prod = np.prod(np.stack([orc.integrand(one[i], X[:, i]) for i in range(3)], 1), 1)
+    np.testing.assert_allclose(orc.integrand(fc, X), prod, rtol=1e-14)
+
+
 @pytest.mark.parametrize("d", [1, 2])
 def test_double_gaussian_quadrature(orc, d):
     c1, c2, w = 1 / 3, 2 / 3, 0.05
