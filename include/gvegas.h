@@ -70,6 +70,9 @@ typedef enum {
  *  VG_GENZ_OSCILLATORY   a[d], u1:    f = cos(2 pi u1 + sum_i a_i x_i)
  *  VG_DOUBLE_GAUSSIAN    c1, c2, w:   f = 1/2 sum_{c in {c1,c2}}
  *                                          (w sqrt pi)^-d exp(-sum_i ((x_i-c)/w)^2)
+ *  VG_GENZ_CONTINUOUS    a[d], u[d]:  f = exp(-sum_i a_i |x_i - u_i|)
+ *  VG_GENZ_DISCONTINUOUS a[d], u[min(d,2)]:  f = exp(sum_i a_i x_i) where
+ *                                          x_1 <= u_1 and x_2 <= u_2, else 0
  *  VG_RAMBO_BW           10 slots (VG_RB_*), d = 4 n:  n massless partons
  *      from RAMBO (4 numbers each), f = V_n * cut(p) * BW(s_12) *
  *      prod_{i} 1/s_{i,i+1 mod n}, with BW(s) = M G / ((s-M^2)^2 + M^2 G^2),
@@ -83,7 +86,9 @@ typedef enum {
   VG_GENZ_CORNER_PEAK = 2,
   VG_GENZ_OSCILLATORY = 3,
   VG_DOUBLE_GAUSSIAN = 4,
-  VG_RAMBO_BW = 5
+  VG_RAMBO_BW = 5,
+  VG_GENZ_CONTINUOUS = 6,
+  VG_GENZ_DISCONTINUOUS = 7
 } vegas_integrand_kind;
 
 enum {

@@ -89,6 +89,8 @@ __device__ __forceinline__ T batch_eval(int kind, const T (&x)[DM], int d, const
     case VG_GENZ_PRODUCT_PEAK: return GenzProductPeak<T, DM>::eval(x, d, P);
     case VG_GENZ_CORNER_PEAK: return GenzCornerPeak<T, DM>::eval(x, d, P);
     case VG_GENZ_OSCILLATORY: return GenzOscillatory<T, DM>::eval(x, d, P);
+    case VG_GENZ_CONTINUOUS: return GenzContinuous<T, DM>::eval(x, d, P);
+    case VG_GENZ_DISCONTINUOUS: return GenzDiscontinuous<T, DM>::eval(x, d, P);
     default: return DoubleGaussian<T, DM>::eval(x, d, P);
   }
 }

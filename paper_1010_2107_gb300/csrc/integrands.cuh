@@ -160,6 +160,35 @@ struct GenzOscillatory {
   }
 };
 
+// f = exp(-sum a_i |x_i - u_i|) (Genz "continuous").  P[i] = a_i,
+// P[kMaxDim+i] = u_i.
+template <typename T, int DM>
+struct GenzContinuous {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    T q = T(0);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) q = vfma(P[a], fabs(x[a] - P[kMaxDim + a]), q);
+    return gexp(-q);
+  }
+};
+
+// f = exp(sum a_i x_i) where x_1 <= u_1 and x_2 <= u_2, else 0 (Genz
+// "discontinuous"; only x_1 for d = 1).  P[i] = a_i, P[kScalar], P[kScalar+1]
+// = u_1, u_2 (u_2 = 2 when d = 1: never binding).
+template <typename T, int DM>
+struct GenzDiscontinuous {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    static_assert(DM >= 2, "compiled bounds start at 4 axes");
+    if (x[0] > P[kScalar] || (d > 1 && x[1] > P[kScalar + 1])) return T(0);
+    T t = T(0);
+#pragma unroll
+    for (int a = 0; a < DM; ++a)
+      if (a < d) t = vfma(P[a], x[a], t);
+    return qexp(t);
+  }
+};
+
 // Two Gaussian peaks (Lepage's test shape), normalised to unit integral over
 // R^d: f = K/2 (exp(-|x - c1|^2 / w^2) + exp(-|x - c2|^2 / w^2)).
 // P[kScalar + 0..3] = c1, c2, 1/w^2, K/2 with K = (w sqrt pi)^-d.

@@ -43,6 +43,10 @@ bool entries_genz_oscillatory_y24(int prec, int d, KernelEntry* out);
 bool entries_genz_oscillatory_y53(int prec, int d, KernelEntry* out);
 bool entries_dgauss_y24(int prec, int d, KernelEntry* out);
 bool entries_dgauss_y53(int prec, int d, KernelEntry* out);
+bool entries_genz_continuous_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_continuous_y53(int prec, int d, KernelEntry* out);
+bool entries_genz_discontinuous_y24(int prec, int d, KernelEntry* out);
+bool entries_genz_discontinuous_y53(int prec, int d, KernelEntry* out);
 bool entries_rambo_y24(int prec, int d, KernelEntry* out);
 bool entries_rambo_y53(int prec, int d, KernelEntry* out);
 

@@ -18,6 +18,8 @@ int expected_nparams(int kind, int d) {
     case VG_GENZ_OSCILLATORY: return d + 1;
     case VG_DOUBLE_GAUSSIAN: return 3;
     case VG_RAMBO_BW: return VG_RB_NPARAMS;
+    case VG_GENZ_CONTINUOUS: return 2 * d;
+    case VG_GENZ_DISCONTINUOUS: return d + (d < 2 ? d : 2);
     default: return -1;
   }
 }
@@ -47,6 +49,17 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale, 
     case VG_GENZ_OSCILLATORY:
       for (int i = 0; i < d; ++i) dv[i] = p[i];
       dv[S] = 2.0 * M_PI * p[d];
+      return true;
+    case VG_GENZ_CONTINUOUS:
+      for (int i = 0; i < d; ++i) {
+        dv[i] = p[i];
+        dv[M + i] = p[d + i];
+      }
+      return true;
+    case VG_GENZ_DISCONTINUOUS:
+      for (int i = 0; i < d; ++i) dv[i] = p[i];
+      dv[S] = p[d];
+      dv[S + 1] = d > 1 ? p[d + 1] : 2.0;
       return true;
     case VG_DOUBLE_GAUSSIAN: {
       const double w = p[2];

@@ -36,6 +36,8 @@ GENZ_CORNER_PEAK = 2
 GENZ_OSCILLATORY = 3
 DOUBLE_GAUSSIAN = 4
 RAMBO_BW = 5
+GENZ_CONTINUOUS = 6
+GENZ_DISCONTINUOUS = 7
 
 # Parameter slots of RAMBO_BW.
 RB_N, RB_SQRTS, RB_M, RB_GAMMA, RB_PTMIN, RB_DRMIN, RB_CUT, RB_T, RB_WC, RB_OBS = range(10)

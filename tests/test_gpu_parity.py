@@ -44,6 +44,8 @@ CASES = [
     ("rb4s", wl.RAMBO_BW, 16, wl.rambo_params(4, cut=1), {}),
     ("dg4strat", wl.DOUBLE_GAUSSIAN, 4, wl.double_gaussian_params(), dict(nstrat=4, ncall=4 ** 4 * 6)),
     ("gauss3strat3", wl.GENZ_GAUSSIAN, 3, wl.genz_gaussian_params(3, a=5.0), dict(nstrat=3, ncall=27 * 37)),
+    ("cont4", wl.GENZ_CONTINUOUS, 4, np.array([3.0, 5.0, 2.0, 4.0, 0.3, 0.6, 0.5, 0.45]), {}),
+    ("disc3", wl.GENZ_DISCONTINUOUS, 3, np.array([1.5, 2.0, 0.7, 0.4, 0.6]), {}),
 ]
 
 
@@ -70,8 +72,10 @@ def test_words_bins_points(gv, orc, name, kind, d, params, kw, precision, ybits)
             else:
                 np.testing.assert_allclose(g["x"], o["x"], rtol=0, atol=3e-7)
                 ok = np.isclose(fg, fo, rtol=2e-4, atol=1e-300 + 1e-6 * np.max(np.abs(fo)))
-            # cut decisions may flip for points within rounding of a cut edge
-            assert np.mean(ok) >= (0.99 if kind == wl.RAMBO_BW else 1.0), np.flatnonzero(~ok)[:10]
+            # cut decisions (and the discontinuous family's edges) may flip for
+            # points within rounding of the edge
+            flips = kind in (wl.RAMBO_BW, wl.GENZ_DISCONTINUOUS)
+            assert np.mean(ok) >= (0.99 if flips else 1.0), np.flatnonzero(~ok)[:10]
 
 
 def _cond_close(a, b, scale, tol):
