@@ -40,8 +40,10 @@
 #ifndef GVEGAS_H
 #define GVEGAS_H
 
+#ifndef __CUDACC_RTC__ /* the run-time compiled kernels see no C library */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -50,6 +52,7 @@ extern "C" {
 #define GVEGAS_MAXDIM 32      /* largest ndim a context accepts            */
 #define GVEGAS_MAXBINS 256    /* largest nbins (grid bins per axis)         */
 #define GVEGAS_MAXHIST 4096   /* iterations kept in one combination window  */
+#define GVEGAS_MAXUSERPARAMS 120 /* parameters of a run-time compiled integrand */
 
 typedef struct vegas_ctx vegas_ctx;
 
@@ -88,7 +91,9 @@ typedef enum {
   VG_DOUBLE_GAUSSIAN = 4,
   VG_RAMBO_BW = 5,
   VG_GENZ_CONTINUOUS = 6,
-  VG_GENZ_DISCONTINUOUS = 7
+  VG_GENZ_DISCONTINUOUS = 7,
+  VG_USER = 64          /* run-time compiled (vegas_create_user); not valid
+                           for vegas_create or the batched and no-alloc calls */
 } vegas_integrand_kind;
 
 enum {
@@ -150,6 +155,8 @@ typedef struct {
   int64_t samples;       /* points evaluated in the current window        */
 } vegas_result;
 
+#ifndef __CUDACC_RTC__ /* the run-time compiled kernels take the types only */
+
 /* Create a context: copies config and integrand, allocates device buffers,
  * sets the uniform grid e_a[k] = k/N (step 1).  Errors: VEGAS_EINVAL for
  * out-of-range sizes or parameter counts, VEGAS_ENOMEM, VEGAS_ECUDA. */
@@ -206,6 +213,34 @@ vegas_status vegas_get_cube_sums(vegas_ctx* ctx, double* sums);
  * exact resume together with vegas_set_grid. */
 vegas_status vegas_get_iteration(vegas_ctx* ctx, uint32_t* it);
 vegas_status vegas_set_iteration(vegas_ctx* ctx, uint32_t it);
+
+/* Create a context for an integrand given as CUDA C++ source, compiled at
+ * run time (NVRTC, sm_103a) into the same sampling, dump and SPRING kernels
+ * the built-in integrands use (step 3 of Sec. 2.1 with the user's f; the
+ * paper's users likewise write their integrand as device code).  `source`
+ * must define, at namespace scope,
+ *
+ *   template <typename T>
+ *   __device__ T vegas_user_f(const T* x, int d, const T* p);
+ *
+ * returning f(x) for the point x[0..d) in (0,1)^d, with p[0..nparams) the
+ * parameters converted to T.  T is double for VG_FP64 and float for the two
+ * FP32 forms.  The source sees the CUDA device built-ins and this library's
+ * device helpers (namespace gv), no C or C++ library headers.  The kernels
+ * are compiled with ndim as their exact dimension; a compiled program is
+ * cached, keyed by (source, precision, ybits, ndim, kernel shape), for the
+ * life of the process.  No adjoint kernel (vegas_grad) is built.  Errors:
+ * VEGAS_EINVAL with the compiler's log in vegas_last_error(NULL) when the
+ * source does not compile, or for bad sizes; VEGAS_ECUDA when the run-time
+ * compiler (libnvrtc) cannot be loaded or the module does not load. */
+vegas_status vegas_create_user(const vegas_config* config, const char* source,
+                               const double* params, int nparams,
+                               vegas_ctx** out);
+
+/* Compile `source` as vegas_create_user would for `config`, without
+ * loading it (needs no device); the program is cached for a later
+ * vegas_create_user.  Errors as there. */
+vegas_status vegas_user_compile(const vegas_config* config, const char* source);
 
 /* Replace the integrand parameters (same count as at creation). */
 vegas_status vegas_set_params(vegas_ctx* ctx, const double* params,
@@ -392,6 +427,8 @@ vegas_status vegas_eval_noalloc(const vegas_config* config, const vegas_integran
 /* Message of the last failure on ctx (or of the calling thread when ctx is
  * NULL).  Never NULL. */
 const char* vegas_last_error(const vegas_ctx* ctx);
+
+#endif /* __CUDACC_RTC__ */
 
 #ifdef __cplusplus
 }

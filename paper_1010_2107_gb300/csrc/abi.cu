@@ -22,14 +22,26 @@
 
 using gv::GState;
 
+static_assert(GVEGAS_MAXUSERPARAMS == gv::kNumDerived, "user parameters fill the derived-constant block");
+
 namespace {
 
 thread_local std::string g_thread_err;
 
 std::string vformat(const char* fmt, va_list ap) {
   char buf[512];
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  return std::string(buf);
+  va_list ap2;
+  va_copy(ap2, ap);
+  const int n = vsnprintf(buf, sizeof buf, fmt, ap);
+  if (n < (int)sizeof buf) {
+    va_end(ap2);
+    return std::string(buf);
+  }
+  std::string big((size_t)n + 1, '\0');
+  vsnprintf(&big[0], big.size(), fmt, ap2);
+  va_end(ap2);
+  big.resize((size_t)n);
+  return big;
 }
 
 }  // namespace
@@ -467,44 +479,9 @@ bool valid_grid(const double* e, int d, int N) {
   return true;
 }
 
-}  // namespace
-
-extern "C" {
-
-const char* vegas_last_error(const vegas_ctx* ctx) {
-  if (ctx) return ctx->err.c_str();
-  return g_thread_err.c_str();
-}
-
-void vegas_destroy(vegas_ctx* c) {
-  if (!c) return;
-  if (c->stream) cudaStreamSynchronize(c->stream);
-  destroy_graphs(c);
-  cudaFree(c->d_edges);
-  cudaFree(c->d_tab64);
-  cudaFree(c->d_tab32);
-  cudaFree(c->d_derived);
-  cudaFree(c->d_part_bins);
-  cudaFree(c->d_part_tot);
-  cudaFree(c->d_bins);
-  cudaFree(c->d_tot);
-  cudaFree(c->d_cubes);
-  cudaFree(c->d_cube_max);
-  for (void* p : {(void*)c->d_q, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
-                  (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
-    cudaFree(p);
-  cudaFree(c->d_gpart);
-  cudaFree(c->d_st);
-  if (c->h_st) cudaFreeHost(c->h_st);
-  if (c->h_stage) cudaFreeHost(c->h_stage);
-  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-  delete c;
-}
-
-vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, vegas_ctx** out) {
-  if (!out) return thread_fail(VEGAS_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!cfg || !fn) return thread_fail(VEGAS_EINVAL, "config or integrand is NULL");
+// Checks on a configuration shared by every constructor: sizes, precision,
+// random bits (ybits, resolved), and the stratification g^d | ncall.
+vegas_status check_config(const vegas_config* cfg, int* ybits_out, int* g_out, uint64_t* G_out) {
   const int d = cfg->ndim, N = cfg->nbins;
   if (d < 1 || d > GVEGAS_MAXDIM) return thread_fail(VEGAS_EINVAL, "ndim %d outside 1..%d", d, GVEGAS_MAXDIM);
   if (N < 2 || N > GVEGAS_MAXBINS) return thread_fail(VEGAS_EINVAL, "nbins %d outside 2..%d", N, GVEGAS_MAXBINS);
@@ -515,11 +492,6 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   const int ybits = cfg->ybits ? cfg->ybits : (cfg->precision == VG_FP64 ? 53 : 24);
   if (ybits != 24 && ybits != 53) return thread_fail(VEGAS_EINVAL, "ybits must be 24 or 53");
   if (!(cfg->alpha >= 0.0) || !std::isfinite(cfg->alpha)) return thread_fail(VEGAS_EINVAL, "alpha must be >= 0");
-  if (fn->ndim != d) return thread_fail(VEGAS_EINVAL, "integrand ndim %d != config ndim %d", fn->ndim, d);
-  const int np = gv::expected_nparams(fn->kind, d);
-  if (np < 0) return thread_fail(VEGAS_EINVAL, "unknown integrand kind %d", fn->kind);
-  if (fn->nparams != np || (np > 0 && !fn->params))
-    return thread_fail(VEGAS_EINVAL, "integrand kind %d needs %d parameters, got %d", fn->kind, np, fn->nparams);
   const int g = cfg->nstrat < 1 ? 1 : cfg->nstrat;
   uint64_t G = 1;
   for (int a = 0; a < d; ++a) {
@@ -530,29 +502,39 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   if (G > 1 && (uint64_t)cfg->ncall / G < 2) return thread_fail(VEGAS_EINVAL, "need >= 2 points per hypercube");
   if ((int64_t)g * N >= (ybits == 53 ? 2048 : (1 << 30)))
     return thread_fail(VEGAS_EINVAL, "nstrat * nbins too large for %d-bit sampling", ybits);
+  *ybits_out = ybits;
+  *g_out = g;
+  *G_out = G;
+  return VEGAS_OK;
+}
 
+vegas_ctx* new_context(const vegas_config* cfg, int ybits, int g, uint64_t G) {
   vegas_ctx* c = new vegas_ctx();
   c->cfg = *cfg;
   c->cfg.ybits = ybits;
-  c->kind = fn->kind;
-  c->params.assign(fn->params, fn->params + np);
   c->prec = cfg->precision;
   c->ybits = ybits;
   c->g = g;
   c->ncubes = G;
   c->nc = (uint64_t)cfg->ncall / G;
   c->strat = G > 1;
-  std::string why;
-  if (!gv::derive_params(fn->kind, d, c->params.data(), c->derived, &c->scale, &why)) {
-    delete c;
-    return thread_fail(VEGAS_EINVAL, "%s", why.c_str());
-  }
-  if (!lookup_kernel(fn->kind, c->prec, ybits, d, &c->ke)) {
-    delete c;
-    return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
-  }
+  return c;
+}
+
+// The specialised sampling kernel applies: d equal to the compile-time bound
+// dm, 24-bit words, a power-of-two number of divisions with g N <= 256.
+bool spec_shape(int d, int dm, int ybits, int g, int N) {
+  return d == dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256;
+}
+
+// Second half of every constructor, for a context whose integrand, kernel
+// entry and constants are set: device buffers, launch shape, uniform grid.
+vegas_status finish_create(vegas_ctx* c, vegas_ctx** out) {
+  const vegas_config* cfg = &c->cfg;
+  const int d = cfg->ndim, N = cfg->nbins;
+  const uint64_t G = c->ncubes;
   // the specialised kernel when the shape allows it (see kernels.h)
-  if (c->ke.sample_spec && d == c->ke.dm && ybits == 24 && (g & (g - 1)) == 0 && (int64_t)g * N <= 256) {
+  if (c->ke.sample_spec && spec_shape(d, c->ke.dm, c->ybits, c->g, N)) {
     c->ke.sample = c->ke.sample_spec;
     c->ppt_min = c->ke.spec_ppt_min;
     if (c->ke.grad_spec) c->ke.grad = c->ke.grad_spec;
@@ -620,6 +602,108 @@ vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, ve
   if ((st = upload_grid(c, e0.data()))) return bail(st);
   if ((st = upload_derived(c))) return bail(st);
   *out = c;
+  return VEGAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vegas_last_error(const vegas_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_thread_err.c_str();
+}
+
+void vegas_destroy(vegas_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  destroy_graphs(c);
+  cudaFree(c->d_edges);
+  cudaFree(c->d_tab64);
+  cudaFree(c->d_tab32);
+  cudaFree(c->d_derived);
+  cudaFree(c->d_part_bins);
+  cudaFree(c->d_part_tot);
+  cudaFree(c->d_bins);
+  cudaFree(c->d_tot);
+  cudaFree(c->d_cubes);
+  cudaFree(c->d_cube_max);
+  for (void* p : {(void*)c->d_q, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
+                  (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
+    cudaFree(p);
+  cudaFree(c->d_gpart);
+  cudaFree(c->d_st);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+vegas_status vegas_create(const vegas_config* cfg, const vegas_integrand* fn, vegas_ctx** out) {
+  if (!out) return thread_fail(VEGAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !fn) return thread_fail(VEGAS_EINVAL, "config or integrand is NULL");
+  int ybits = 0, g = 1;
+  uint64_t G = 1;
+  vegas_status cs = check_config(cfg, &ybits, &g, &G);
+  if (cs) return cs;
+  const int d = cfg->ndim;
+  if (fn->ndim != d) return thread_fail(VEGAS_EINVAL, "integrand ndim %d != config ndim %d", fn->ndim, d);
+  const int np = gv::expected_nparams(fn->kind, d);
+  if (np < 0) return thread_fail(VEGAS_EINVAL, "unknown integrand kind %d", fn->kind);
+  if (fn->nparams != np || (np > 0 && !fn->params))
+    return thread_fail(VEGAS_EINVAL, "integrand kind %d needs %d parameters, got %d", fn->kind, np, fn->nparams);
+  vegas_ctx* c = new_context(cfg, ybits, g, G);
+  c->kind = fn->kind;
+  c->params.assign(fn->params, fn->params + np);
+  std::string why;
+  if (!gv::derive_params(fn->kind, d, c->params.data(), c->derived, &c->scale, &why)) {
+    delete c;
+    return thread_fail(VEGAS_EINVAL, "%s", why.c_str());
+  }
+  if (!lookup_kernel(fn->kind, c->prec, ybits, d, &c->ke)) {
+    delete c;
+    return thread_fail(VEGAS_EINVAL, "no kernel for kind %d, ndim %d", fn->kind, d);
+  }
+  return finish_create(c, out);
+}
+
+vegas_status vegas_create_user(const vegas_config* cfg, const char* source, const double* params, int nparams,
+                               vegas_ctx** out) {
+  if (!out) return thread_fail(VEGAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !source) return thread_fail(VEGAS_EINVAL, "config or source is NULL");
+  int ybits = 0, g = 1;
+  uint64_t G = 1;
+  vegas_status cs = check_config(cfg, &ybits, &g, &G);
+  if (cs) return cs;
+  if (nparams < 0 || nparams > GVEGAS_MAXUSERPARAMS || (nparams > 0 && !params))
+    return thread_fail(VEGAS_EINVAL, "user integrand takes 0..%d parameters, got %d", GVEGAS_MAXUSERPARAMS, nparams);
+  vegas_ctx* c = new_context(cfg, ybits, g, G);
+  c->kind = VG_USER;
+  c->params.assign(params, params + nparams);
+  std::copy(c->params.begin(), c->params.end(), c->derived);
+  c->scale = 1.0;
+  std::string why;
+  const int d = cfg->ndim;
+  const int rs = gv::rtc_user_entry(source, c->prec, ybits, d, spec_shape(d, d, ybits, g, cfg->nbins), &c->ke, &why);
+  if (rs != VEGAS_OK) {
+    delete c;
+    return thread_fail((vegas_status)rs, "%s", why.c_str());
+  }
+  return finish_create(c, out);
+}
+
+vegas_status vegas_user_compile(const vegas_config* cfg, const char* source) {
+  if (!cfg || !source) return thread_fail(VEGAS_EINVAL, "config or source is NULL");
+  int ybits = 0, g = 1;
+  uint64_t G = 1;
+  vegas_status cs = check_config(cfg, &ybits, &g, &G);
+  if (cs) return cs;
+  const int d = cfg->ndim;
+  std::string why;
+  const int rs = gv::rtc_user_compile(source, cfg->precision, ybits, d, spec_shape(d, d, ybits, g, cfg->nbins), &why);
+  if (rs != VEGAS_OK) return thread_fail((vegas_status)rs, "%s", why.c_str());
   return VEGAS_OK;
 }
 
@@ -909,9 +993,11 @@ vegas_status vegas_set_params(vegas_ctx* c, const double* params, int nparams) {
   if (!params || nparams != (int)c->params.size())
     return c->fail(VEGAS_EINVAL, "expected %d parameters", (int)c->params.size());
   std::vector<double> p(params, params + nparams);
-  double dv[gv::kNumDerived], sc;
+  double dv[gv::kNumDerived] = {}, sc = 1.0;
   std::string why;
-  if (!gv::derive_params(c->kind, c->cfg.ndim, p.data(), dv, &sc, &why))
+  if (c->kind == VG_USER)  // the user's parameters are the device constants
+    std::copy(p.begin(), p.end(), dv);
+  else if (!gv::derive_params(c->kind, c->cfg.ndim, p.data(), dv, &sc, &why))
     return c->fail(VEGAS_EINVAL, "%s", why.c_str());
   c->params = p;
   memcpy(c->derived, dv, sizeof dv);

@@ -3,8 +3,19 @@
 // and the argument blocks of the kernels.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Run-time compilation (user integrands, see rtc.cu): no host headers, so
+// the fixed-width types are spelled out (LP64, as on the host side).
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long int64_t;
+typedef unsigned long uint64_t;
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "../../include/gvegas.h"
 

@@ -3,14 +3,18 @@
 // the reduction / finalisation kernels.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <stddef.h>
 
 #include <string>
+#endif
 
 #include "common.cuh"
 
 namespace gv {
+
+#ifndef __CUDACC_RTC__  // host side only (run-time compiled kernels see the argument blocks)
 
 // One compiled sampling kernel and its companions for a (kind, precision, DM).
 struct KernelEntry {
@@ -55,6 +59,16 @@ bool entries_rambo_y53(int prec, int d, KernelEntry* out);
 // kNumDerived) plus the output scale; false with a reason when invalid.
 int expected_nparams(int kind, int d);
 bool derive_params(int kind, int d, const double* p, double* dv, double* scale, std::string* why);
+
+// Kernels of a run-time compiled integrand (rtc.cu) with exact dimension
+// d: the specialised sampling and SPRING kernels when `spec` (the shape
+// allows them), else the general ones, plus the dump kernel.  Returns
+// VEGAS_OK, VEGAS_EINVAL (the source does not compile: *why holds the
+// compiler's log) or VEGAS_ECUDA (no run-time compiler, or the module does
+// not load).
+int rtc_user_entry(const char* source, int prec, int ybits, int d, bool spec, KernelEntry* out, std::string* why);
+// The same compile without loading (no device needed); the result is cached.
+int rtc_user_compile(const char* source, int prec, int ybits, int d, bool spec, std::string* why);
 
 // Histogram tile of a sampling kernel: ppt points per thread between two
 // gathers, bucket capacity cap per (axis, bin), and the CTAs per SM that
@@ -126,6 +140,8 @@ inline int choose_lanes(uint64_t G, uint64_t nc, int threads, int64_t ctas) {
   return L;
 }
 
+#endif  // __CUDACC_RTC__
+
 // Arguments of the SPRING trial kernel: trials trial0 .. trial0 + n - 1 in
 // chunks of `chunk` trials; the kept points of chunk k go, in trial order, to
 // stage_x[(k chunk + i) d + a] and stage_t[k chunk + i], their number to
@@ -157,6 +173,7 @@ struct DumpArgs {
 
 }  // namespace gv
 
+#ifndef __CUDACC_RTC__
 extern "C" {
 cudaError_t gv_prepare_aux_kernels(void);
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s);
@@ -166,3 +183,4 @@ cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s);
 cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,
                              cudaStream_t s);
 }
+#endif  // __CUDACC_RTC__

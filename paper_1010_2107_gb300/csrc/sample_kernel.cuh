@@ -10,7 +10,17 @@
 // 53 random bits per axis).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// run-time compilation sees no C++ library: the two traits used here
+namespace std {
+template <class A, class B> struct is_same { static constexpr bool value = false; };
+template <class A> struct is_same<A, A> { static constexpr bool value = true; };
+template <bool C, class A, class B> struct conditional { using type = A; };
+template <class A, class B> struct conditional<false, A, B> { using type = B; };
+}  // namespace std
+#else
 #include <type_traits>
+#endif
 
 #include "common.cuh"
 #include "integrands.cuh"
@@ -665,7 +675,7 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
 }
 
 template <typename T, int ACC>
-inline size_t sample_smem_bytes(int d, int N, int cap) {
+__host__ __device__ inline size_t sample_smem_bytes(int d, int N, int cap) {
   return SmemLayout<T, ACC>::total(d * N, cap);
 }
 
@@ -936,6 +946,8 @@ __global__ void __launch_bounds__(256) k_grad(const SampleArgs A, double* part) 
   }
 }
 
+#ifndef __CUDACC_RTC__  // host-side registry builders
+
 template <typename T>
 inline size_t grad_smem_bytes(int d, int N) {
   return (size_t)d * N * sizeof(typename Vec2<T>::type) + kNumDerived * sizeof(T);
@@ -1009,5 +1021,7 @@ inline bool pick_pow2_bound(int prec, int ybits, int d, KernelEntry* out) {
   if (d <= 32) return pick_precision<F, 32>(prec, ybits, out);
   return false;
 }
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace gv

@@ -19,7 +19,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgvegas.so")
 # vegas_status
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, ESTATE = range(7)
 # vegas_integrand_kind
-GENZ_GAUSSIAN, GENZ_PRODUCT_PEAK, GENZ_CORNER_PEAK, GENZ_OSCILLATORY, DOUBLE_GAUSSIAN, RAMBO_BW = range(6)
+(GENZ_GAUSSIAN, GENZ_PRODUCT_PEAK, GENZ_CORNER_PEAK, GENZ_OSCILLATORY, DOUBLE_GAUSSIAN, RAMBO_BW,
+ GENZ_CONTINUOUS, GENZ_DISCONTINUOUS) = range(8)
+USER = 64  # run-time compiled integrand (vegas_create_user)
+MAXUSERPARAMS = 120
 # vegas_precision
 FP64, FP32_ACC64, FP32_ACCCOMP = range(3)
 PRECISIONS = {"fp64": FP64, "fp32_acc64": FP32_ACC64, "fp32": FP32_ACCCOMP,
@@ -61,6 +64,9 @@ _DP = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "vegas_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
                                     ctypes.POINTER(_P)]),
+    "vegas_create_user": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_char_p, _DP, ctypes.c_int,
+                                         ctypes.POINTER(_P)]),
+    "vegas_user_compile": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_char_p]),
     "vegas_destroy": (None, [_P]),
     "vegas_iterate": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result)]),
     "vegas_reset_results": (ctypes.c_int, [_P]),
@@ -188,6 +194,38 @@ def vegas_create(kind: int, ndim: int, params, *, nbins: int = 50, ncall: int = 
     _check(lib().vegas_create(ctypes.byref(cfg), ctypes.byref(fn), ctypes.byref(h)))
     yb = ybits or (53 if precision == FP64 else 24)
     return Context(h, int(ndim), int(nbins), int(ncall), int(nstrat), yb)
+
+
+def _config(ndim, nbins, ncall, itmx, acc, alpha, nstrat, seed, instance, precision, ybits, stream):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    return Config(int(ndim), int(nbins), int(ncall), int(itmx), float(acc), float(alpha),
+                  int(nstrat), int(seed), int(instance), int(precision), int(ybits),
+                  _stream_handle(stream))
+
+
+def vegas_create_user(source: str, ndim: int, params=(), *, nbins: int = 50, ncall: int = 100_000,
+                      itmx: int = 5, acc: float = 0.0, alpha: float = 1.5, nstrat: int = 0,
+                      seed: int = 1, instance: int = 0, precision=FP64, ybits: int = 0,
+                      stream=None) -> Context:
+    """Context for an integrand given as CUDA source defining
+    ``template <typename T> __device__ T vegas_user_f(const T* x, int d, const T* p)``,
+    compiled at run time (see include/gvegas.h)."""
+    cfg = _config(ndim, nbins, ncall, itmx, acc, alpha, nstrat, seed, instance, precision, ybits, stream)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    h = _P()
+    _check(lib().vegas_create_user(ctypes.byref(cfg), source.encode(), _dp(p) if len(p) else None, len(p),
+                                   ctypes.byref(h)))
+    yb = ybits or (53 if cfg.precision == FP64 else 24)
+    return Context(h, int(ndim), int(nbins), int(ncall), int(nstrat), yb)
+
+
+def vegas_user_compile(source: str, ndim: int, *, nbins: int = 50, ncall: int = 100_000, nstrat: int = 0,
+                       precision=FP64, ybits: int = 0) -> None:
+    """Compile a user integrand for this shape without a device; raises VegasError
+    (EINVAL, with the compiler's log) when the source does not compile."""
+    cfg = _config(ndim, nbins, ncall, 5, 0.0, 1.5, nstrat, 1, 0, precision, ybits, None)
+    _check(lib().vegas_user_compile(ctypes.byref(cfg), source.encode()))
 
 
 def vegas_destroy(ctx: Context):
