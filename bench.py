@@ -41,6 +41,8 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # work; the peak is the FP32 issue rate of all SMs at the maximum clock).
 ALGO_OPS = {
     "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, accumulate=8 * 2 + 2 + 12),
+    "user_dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8,
+                         accumulate=8 * 2 + 2 + 12),
     "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),
     "rambo5": dict(philox=5 * 10 * 6, bins=20 * 6, map=20 * 3, integrand=5 * 60 + 10 * 8 + 5 * 14 + 10,
                    accumulate=20 * 2 + 14),
@@ -60,6 +62,12 @@ TRAFFIC = {"dgauss8": 68096}
 def _workload(name):
     from paper_1010_2107_gb300 import workloads as wl
     return wl.WORKLOADS[name]
+
+
+def _oracle_integrand(w):
+    """The oracle's integrand of a workload (a user source's built-in twin)."""
+    import oracle
+    return oracle.Integrand(w.get("oracle_kind", w["kind"]), w["ndim"], w.get("oracle_params", w["params"]))
 
 
 def _measured_peaks():
@@ -164,7 +172,7 @@ def oracle_rate(name: str, iters_refine: int, iters_frozen: int):
     d = w["ndim"]
     cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
                           seed=w["seed"])
-    fn = oracle.Integrand(w["kind"], d, w["params"])
+    fn = _oracle_integrand(w)
     e = oracle.uniform_grid(d, w["nbins"])
     t = time.perf_counter()
     if w.get("mode") == "bases":
@@ -184,7 +192,7 @@ def oracle_spring_rate(R, h, n=1 << 20):
     d = w["ndim"]
     cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
                           seed=w["seed"])
-    fn = oracle.Integrand(w["kind"], d, w["params"])
+    fn = _oracle_integrand(w)
     edges, cmax = gv.vegas_get_grid(h), gv.vegas_get_cube_max(h)
     t = time.perf_counter()
     oracle.spring(cfg, fn, edges, cmax, 0, n)
@@ -202,7 +210,7 @@ def _oracle_worker(job):
     d = w["ndim"]
     cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
                           seed=w["seed"], instance=instance)
-    fn = oracle.Integrand(w["kind"], d, w["params"])
+    fn = _oracle_integrand(w)
     oracle.vegas(cfg, fn, oracle.uniform_grid(d, w["nbins"]), 0, 1)  # untimed warm-up
     e = oracle.uniform_grid(d, w["nbins"])
     t = time.perf_counter()
@@ -254,7 +262,7 @@ def _reference_step(name):
         d = w["ndim"]
         cfg = oracle.make_cfg(d, nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], ybits=w["ybits"],
                               seed=w["seed"])
-        fn = oracle.Integrand(w["kind"], d, w["params"])
+        fn = _oracle_integrand(w)
         e = oracle.uniform_grid(d, w["nbins"])
         cmax = oracle.iteration(cfg, fn, e, 0, cubes=True)["Cmax"]  # bounds from one iteration
         n = 1 << 20
@@ -311,7 +319,8 @@ def _config(name):
                 "iterations": wl.GENZ256["itmx"], "l2": "flushed between steps (512 MiB write)"}
     w = _workload(name)
     c = {"workload": name, "ndim": w["ndim"], "nbins": w["nbins"], "ncall": w["ncall"],
-         "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw"}[w["kind"]],
+         "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw",
+                       64: "double_gaussian as run-time compiled CUDA source"}[w["kind"]],
          "precision": w["precision"], "ybits": w["ybits"], "nstrat": w["nstrat"],
          "l2": "flushed between steps (512 MiB write)"}
     if w.get("mode") == "spring":
@@ -372,9 +381,13 @@ class Runner:
             tuned = gv.vegas_batch_autotune(h)
             self.tuned = self.tuned or tuned
             return h
-        h = gv.vegas_create(w["kind"], w["ndim"], w["params"], nbins=w["nbins"], ncall=w["ncall"],
-                            nstrat=w["nstrat"], seed=w["seed"], instance=rank_instance(0, self.rank, self.mode),
-                            precision=prec, ybits=w["ybits"], stream=self.stream)
+        kw = dict(nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], seed=w["seed"],
+                  instance=rank_instance(0, self.rank, self.mode), precision=prec, ybits=w["ybits"],
+                  stream=self.stream)
+        if w.get("source"):
+            h = gv.vegas_create_user(w["source"], w["ndim"], w["params"], **kw)
+        else:
+            h = gv.vegas_create(w["kind"], w["ndim"], w["params"], **kw)
         if self.mode == "adjoint":  # the grid the gradient is taken on
             gv.vegas_iterate(h, w["warmup_iters"], refine=True)
         elif self.mode == "spring":  # the BASES run whose integration phase bounds the cubes
@@ -688,7 +701,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dgauss8",
-                    choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256", "spring_dgauss8"])
+                    choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256", "spring_dgauss8",
+                             "user_dgauss8"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

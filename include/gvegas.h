@@ -321,7 +321,9 @@ vegas_status vegas_get_tile(vegas_ctx* ctx, int* points_per_thread, int* cap);
  * times evaluation passes (as vegas_profile_pass: no refinement, window
  * untouched) for threads per CTA in {128, 256, 384, 512} and histogram
  * tiles in {automatic, 1, 2, 4} points per thread, skipping shapes the
- * kernel cannot take, and keeps the fastest.  Returns its threads, points
+ * kernel cannot take; the three fastest are timed again in three
+ * interleaved rounds of five passes, and the one with the best round is
+ * kept.  Returns its threads, points
  * per thread and the pass time in ms (any output may be NULL).  The
  * specialised kernels (d = the compiled bound, 24-bit words, power-of-two
  * strata) accept up to 512 threads, the general ones 256.  Synchronises the
@@ -376,7 +378,8 @@ vegas_status vegas_batch_set_launch(vegas_batch* batch, int threads, int rounds)
 vegas_status vegas_batch_get_launch(vegas_batch* batch, int* threads, int* rounds, int* ctas, int* items);
 
 /* Autotuner: times every (threads, rounds) candidate on the batch's own
- * workload (an evaluation pass, nothing recorded) and keeps the fastest;
+ * workload (an evaluation pass, nothing recorded), times the three fastest
+ * again in three interleaved rounds and keeps the one with the best round;
  * returns it and its sampling-kernel milliseconds. */
 vegas_status vegas_batch_autotune(vegas_batch* batch, int* threads, int* rounds, double* ms);
 

@@ -33,6 +33,11 @@ DOUBLE_GAUSSIAN = 4
 RAMBO_BW = 5
 GENZ_CONTINUOUS = 6
 GENZ_DISCONTINUOUS = 7
+W_MUNU = 8
+# slots of the W_MUNU parameter vector (oracle.h)
+(W_SQRTS, W_M, W_GAMMA, W_GF, W_VUD, W_PTMIN, W_ETAMAX, W_SMIN, W_CUTS,
+ W_AU, W_ALU, W_BU, W_AD, W_ALD, W_BD) = range(15)
+W_NPARAMS = 15
 
 _lock = threading.Lock()
 _lib = None

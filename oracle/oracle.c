@@ -354,6 +354,7 @@ static int fn_valid(const orc_fn* fn) {
     case ORC_DOUBLE_GAUSSIAN: return fn->nparams >= 3;
     case ORC_GENZ_CONTINUOUS: return fn->nparams >= 2 * d;
     case ORC_GENZ_DISCONTINUOUS: return fn->nparams >= d + (d < 2 ? d : 2);
+    case ORC_W_MUNU: return d == 5 && fn->nparams >= ORC_W_NPARAMS;
     case ORC_RAMBO_BW: {
       if (fn->nparams < ORC_RB_NPARAMS) return 0;
       int n = (int)fn->params[ORC_RB_N];
@@ -361,6 +362,54 @@ static int fn_valid(const orc_fn* fn) {
     }
     default: return 0;
   }
+}
+
+/* u dbar -> W+ -> mu+ nu_mu (see oracle.h for the variables).  Written as
+ * the textbook pieces, in this order: the mapping of y to (shat, y_W,
+ * cos theta, phi, h) with its Jacobian, the parton luminosity, the flux
+ * 1/(2 shat), the two-body phase space dPhi_2 = dcos(theta) dphi / (32
+ * pi^2), and the helicity amplitude squared, sampled over the 16
+ * helicity combinations with weight 16.  For massless V - A couplings only
+ * u(-) dbar(+) -> nu(-) mu+(+) is non-zero:
+ *   |M|^2 = g^4 |V_ud|^2 uhat^2 / ((shat - M^2)^2 + M^2 Gamma^2),
+ *   uhat = (p_u - p_mu)^2,  g^2 = 8 M^2 G_F / sqrt(2),
+ * averaged over the initial spins (1/4) and colours (3 / 9). */
+static double w_munu(const double* P, const double* y) {
+  const double S = P[ORC_W_SQRTS] * P[ORC_W_SQRTS], M = P[ORC_W_M], G = P[ORC_W_GAMMA];
+  const double rho_lo = atan((P[ORC_W_SMIN] - M * M) / (M * G)), rho_hi = atan((S - M * M) / (M * G));
+  const double rho = rho_lo + (rho_hi - rho_lo) * y[0];
+  const double shat = M * M + M * G * tan(rho);
+  const double dshat = (rho_hi - rho_lo) * M * G / (cos(rho) * cos(rho)); /* dshat/dy1 */
+  const double tau = shat / S;
+  if (!(tau > 0.0 && tau < 1.0)) return 0.0;
+  const double L = -log(tau);
+  const double yw = (y[1] - 0.5) * L; /* dyw/dy2 = L */
+  const double x1 = sqrt(tau) * exp(yw), x2 = sqrt(tau) * exp(-yw);
+  if (!(x1 < 1.0 && x2 < 1.0)) return 0.0;
+  const double c = 2.0 * y[2] - 1.0; /* dc/dy3 = 2 */
+  /* phi = 2 pi y4: nothing depends on it; dphi/dy4 = 2 pi */
+  int h = (int)floor(16.0 * y[4]);
+  if (h > 15) h = 15;
+  if (P[ORC_W_CUTS] != 0.0) {
+    const double pt = 0.5 * sqrt(shat) * sqrt(1.0 - c * c);
+    const double eta = atanh(c) + yw; /* partonic rapidity of the mu+ plus the boost */
+    if (!(pt > P[ORC_W_PTMIN] && fabs(eta) < P[ORC_W_ETAMAX])) return 0.0;
+  }
+  /* helicity bits: u, dbar, nu, mu+ (1 = positive helicity) */
+  double msq = 0.0;
+  if (h == (0 | 2 | 0 | 8)) {
+    const double g2 = 8.0 * M * M * P[ORC_W_GF] / sqrt(2.0);
+    const double uhat = -0.5 * shat * (1.0 - c);
+    const double den = (shat - M * M) * (shat - M * M) + M * M * G * G;
+    msq = g2 * g2 * P[ORC_W_VUD] * P[ORC_W_VUD] * uhat * uhat / den;
+  }
+  const double avg = 1.0 / 4.0 * 3.0 / 9.0;
+  const double fu = P[ORC_W_AU] * pow(x1, P[ORC_W_ALU]) * pow(1.0 - x1, P[ORC_W_BU]);
+  const double fd = P[ORC_W_AD] * pow(x2, P[ORC_W_ALD]) * pow(1.0 - x2, P[ORC_W_BD]);
+  const double jac = dshat / S * L * 2.0 * 2.0 * M_PI; /* dtau dyw dc dphi per dy1..dy4 */
+  const double dphi2 = 1.0 / (32.0 * M_PI * M_PI);
+  const double pb = 0.3893793721e9; /* GeV^-2 -> pb */
+  return fu * fd * jac * dphi2 / (2.0 * shat) * 16.0 * avg * msq * pb;
 }
 
 /* One point: f(x) and, when grad != NULL, df/dtheta. */
@@ -441,6 +490,8 @@ static double eval_point(const orc_fn* fn, const double* x, double* grad) {
       }
       return f;
     }
+    case ORC_W_MUNU:
+      return w_munu(P, x);
     case ORC_RAMBO_BW: {
       int n = (int)P[ORC_RB_N];
       double sqrt_s = P[ORC_RB_SQRTS];

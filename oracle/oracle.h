@@ -42,7 +42,33 @@ enum {
   ORC_DOUBLE_GAUSSIAN = 4,   /* params: c1, c2, w                           */
   ORC_RAMBO_BW = 5,          /* params: see ORC_RB_* below, d = 4 n         */
   ORC_GENZ_CONTINUOUS = 6,   /* params: a[d], u[d]                          */
-  ORC_GENZ_DISCONTINUOUS = 7 /* params: a[d], u[min(d, 2)]                  */
+  ORC_GENZ_DISCONTINUOUS = 7, /* params: a[d], u[min(d, 2)]                 */
+  ORC_W_MUNU = 8              /* params: see ORC_W_* below, d = 5             */
+};
+
+/* u dbar -> W+ -> mu+ nu_mu in pp collisions (Sec. 4, the process with
+ * n = 0 gluons and the lepton cuts |eta| < 2.5, pT > 20 GeV), total cross
+ * section in pb.  The five variables: y1 -> shat through the Breit-Wigner
+ * mapping shat = M^2 + M Gamma tan(rho), rho uniform between the images of
+ * [SHAT_MIN, S]; y2 -> the W rapidity, uniform in [ln(tau)/2, -ln(tau)/2];
+ * y3 -> cos(theta) of the mu+ against the u direction in the partonic
+ * frame; y4 -> its azimuth; y5 -> one of 16 helicity combinations (Sec. 4:
+ * one variable sums the helicities).  The u comes from the proton moving
+ * along +z, the dbar from the other.  Parton densities are a stand-in with
+ * the shape f(x) = A x^a (1 - x)^b (no CTEQ6L1 table is available). */
+enum {
+  ORC_W_SQRTS = 0,   /* hadronic centre-of-mass energy sqrt(S), GeV    */
+  ORC_W_M = 1,       /* W mass, GeV                                    */
+  ORC_W_GAMMA = 2,   /* W width, GeV                                   */
+  ORC_W_GF = 3,      /* Fermi constant, GeV^-2                         */
+  ORC_W_VUD = 4,     /* |V_ud|                                         */
+  ORC_W_PTMIN = 5,   /* mu+ transverse momentum cut, GeV               */
+  ORC_W_ETAMAX = 6,  /* mu+ pseudorapidity cut                         */
+  ORC_W_SMIN = 7,    /* lower end of the shat range, GeV^2             */
+  ORC_W_CUTS = 8,    /* 1: apply the two cuts, 0: none                 */
+  ORC_W_AU = 9, ORC_W_ALU = 10, ORC_W_BU = 11,  /* u density A, a, b    */
+  ORC_W_AD = 12, ORC_W_ALD = 13, ORC_W_BD = 14, /* dbar density A, a, b */
+  ORC_W_NPARAMS = 15
 };
 
 /* RAMBO + Breit-Wigner parameter slots. */

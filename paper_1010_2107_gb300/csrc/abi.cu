@@ -1119,29 +1119,47 @@ vegas_status vegas_autotune(vegas_ctx* c, int* threads, int* points_per_thread, 
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
   static const int kThreads[] = {128, 256, 384, 512};
   static const int kTiles[] = {0, 1, 2, 4};
-  const int t0 = c->threads, p0 = c->ppt_req;
-  int best_t = t0, best_p = p0;
-  double best = 1e300;
+  struct Cand {
+    int t, p;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  // one pass of warm-up, then the mean of n passes, for shape (t, p)
+  auto time_shape = [&](int t, int p, int n, double* out) -> vegas_status {
+    if (vegas_set_launch(c, t, 0) != VEGAS_OK || vegas_set_tile(c, p) != VEGAS_OK) return VEGAS_EINVAL;
+    double m[3];
+    vegas_status st = vegas_profile_pass(c, 1, m);
+    if (!st) st = vegas_profile_pass(c, n, m);
+    if (!st) *out = m[2];
+    return st == VEGAS_OK ? VEGAS_OK : VEGAS_ECUDA;
+  };
+  // screening: every shape the kernel takes (the others are skipped)
   for (int t : kThreads)
     for (int p : kTiles) {
-      // shapes the kernel cannot take are skipped, not errors
-      if (vegas_set_launch(c, t, 0) != VEGAS_OK || vegas_set_tile(c, p) != VEGAS_OK) continue;
-      double m[3];
-      vegas_status st = vegas_profile_pass(c, 1, m);  // warm-up
-      if (!st) st = vegas_profile_pass(c, 3, m);
-      if (st) return st;
-      if (m[2] < best) {
-        best = m[2];
-        best_t = t;
-        best_p = p;
-      }
+      double m = 0.0;
+      const vegas_status st = time_shape(t, p, 3, &m);
+      if (st == VEGAS_ECUDA) return c->err.empty() ? c->fail(st, "autotune: pass failed") : st;
+      if (st == VEGAS_OK) cands.push_back({t, p, m});
     }
-  vegas_status st = vegas_set_launch(c, best_t, 0);
-  if (!st) st = vegas_set_tile(c, best_p);
+  if (cands.empty()) return c->fail(VEGAS_EINVAL, "autotune: no launch shape fits");
+  // the three fastest again, in interleaved rounds, keeping each one's best
+  // round (shapes a few percent apart are within one screening's noise)
+  std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.ms < b.ms; });
+  cands.resize(std::min<size_t>(cands.size(), 3));
+  for (int r = 0; r < 3; ++r)
+    for (Cand& k : cands) {
+      double m = 0.0;
+      if (time_shape(k.t, k.p, 5, &m) != VEGAS_OK) return c->fail(VEGAS_ECUDA, "autotune: pass failed");
+      k.ms = r == 0 ? m : std::min(k.ms, m);
+    }
+  const Cand best = *std::min_element(cands.begin(), cands.end(),
+                                      [](const Cand& a, const Cand& b) { return a.ms < b.ms; });
+  vegas_status st = vegas_set_launch(c, best.t, 0);
+  if (!st) st = vegas_set_tile(c, best.p);
   if (st) return st;
-  if (threads) *threads = best_t;
+  if (threads) *threads = best.t;
   if (points_per_thread) *points_per_thread = c->ppt;
-  if (ms) *ms = best;
+  if (ms) *ms = best.ms;
   return VEGAS_OK;
 }
 

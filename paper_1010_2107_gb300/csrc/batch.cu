@@ -887,26 +887,44 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   if (!b) return bfail("batch is NULL");
   static const int kThreads[] = {128, 256};
   static const int kRounds[] = {8, 16, 32, 64, 128};
-  int best_t = b->threads, best_r = b->rounds;
-  double best = 1e300;
+  struct Cand {
+    int t, r;
+    double ms;
+  };
+  std::vector<Cand> cands;
+  // one warm-up pass, then the mean of n passes, for shape (t, r)
+  auto time_shape = [&](int t, int r, int n, double* out) -> vegas_status {
+    vegas_status st = vegas_batch_set_launch(b, t, r);
+    double m[2];
+    if (!st) st = vegas_batch_profile(b, 1, m);
+    if (!st) st = vegas_batch_profile(b, n, m);
+    if (!st) *out = m[0];
+    return st;
+  };
   for (int t : kThreads)
     for (int r : kRounds) {
-      vegas_status st = vegas_batch_set_launch(b, t, r);
+      double m = 0.0;
+      vegas_status st = time_shape(t, r, 3, &m);
       if (st) return st;
-      double m[2];
-      if ((st = vegas_batch_profile(b, 1, m))) return st;  // warm-up
-      if ((st = vegas_batch_profile(b, 3, m))) return st;
-      if (m[0] < best) {
-        best = m[0];
-        best_t = t;
-        best_r = r;
-      }
+      cands.push_back({t, r, m});
     }
-  vegas_status st = vegas_batch_set_launch(b, best_t, best_r);
+  // the three fastest again in interleaved rounds, keeping each one's best
+  std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
+  cands.resize(std::min<size_t>(cands.size(), 3));
+  for (int k = 0; k < 3; ++k)
+    for (Cand& c : cands) {
+      double m = 0.0;
+      vegas_status st = time_shape(c.t, c.r, 3, &m);
+      if (st) return st;
+      c.ms = k == 0 ? m : std::min(c.ms, m);
+    }
+  const Cand best = *std::min_element(cands.begin(), cands.end(),
+                                      [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
+  vegas_status st = vegas_batch_set_launch(b, best.t, best.r);
   if (st) return st;
-  if (threads) *threads = best_t;
-  if (rounds) *rounds = best_r;
-  if (ms) *ms = best;
+  if (threads) *threads = best.t;
+  if (rounds) *rounds = best.r;
+  if (ms) *ms = best.ms;
   return VEGAS_OK;
 }
 

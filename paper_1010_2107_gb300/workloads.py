@@ -1,7 +1,7 @@
 """Seeded synthetic workloads: shapes, sizes and integrand parameter vectors.
 
 This module holds no arithmetic of the integration method.  It only states the
-five workloads (sizes, seeds, parameter vectors) and draws the parameters of the
+workloads (sizes, seeds, parameter vectors) and draws the parameters of the
 batched Genz workload from numpy's PCG64 generator.  Both the CUDA library's
 callers and the CPU oracle's tests take their inputs from here.
 
@@ -19,6 +19,8 @@ iterations, BASES split ITMX1 = ITMX2 with ITMX1 + ITMX2 = ITMX):
 * ``rambo4_adjoint``  2->4 RAMBO (16 dims), sigmoid pT cut (T = 20 GeV,
                width 1 GeV); gradient in (M, Gamma, T) on 2^24 points after a
                5-iteration grid warm-up.
+* ``user_dgauss8``  ``dgauss8`` with the integrand given as CUDA source
+               (``DGAUSS_USER_SOURCE``) and compiled at run time.
 * ``genz256``  256 Genz integrands (product peak, corner peak, oscillatory),
                d uniform in 2..16, points per instance log-uniform in
                2^16..2^22, 8 iterations each.
@@ -38,6 +40,8 @@ DOUBLE_GAUSSIAN = 4
 RAMBO_BW = 5
 GENZ_CONTINUOUS = 6
 GENZ_DISCONTINUOUS = 7
+W_MUNU = 8
+USER = 64  # run-time compiled source
 
 # Parameter slots of RAMBO_BW.
 RB_N, RB_SQRTS, RB_M, RB_GAMMA, RB_PTMIN, RB_DRMIN, RB_CUT, RB_T, RB_WC, RB_OBS = range(10)
@@ -57,6 +61,51 @@ def genz_gaussian_params(d: int, a: float = 10.0, u: float = 0.5) -> np.ndarray:
 def double_gaussian_params(c1: float = 1.0 / 3.0, c2: float = 2.0 / 3.0,
                            w: float = 0.05) -> np.ndarray:
     return np.array([c1, c2, w], dtype=np.float64)
+
+
+# Parameter slots of W_MUNU (include/gvegas.h).
+(W_SQRTS, W_M, W_GAMMA, W_GF, W_VUD, W_PTMIN, W_ETAMAX, W_SMIN, W_CUTS,
+ W_AU, W_ALU, W_BU, W_AD, W_ALD, W_BD) = range(15)
+W_NPARAMS = 15
+
+
+def w_munu_params(sqrt_s: float = 14000.0, M: float = 80.4, Gamma: float = 2.1,
+                  GF: float = 1.16639e-5, Vud: float = 0.974, ptmin: float = 20.0,
+                  etamax: float = 2.5, smin: float | None = None, cuts: int = 1,
+                  u_pdf=(2.0, -0.5, 3.0), dbar_pdf=(0.15, -1.15, 7.0)) -> np.ndarray:
+    """u dbar -> W+ -> mu+ nu at the LHC energy of Sec. 5 with the lepton cuts
+    of Sec. 4.  The parton densities are a stand-in, A x^a (1 - x)^b for u
+    (valence-like) and dbar (sea-like), since no PDF table is available.
+    The shat range starts at smin, by default (2 ptmin)^2, below which no
+    mu+ passes the pT cut."""
+    p = np.zeros(W_NPARAMS)
+    p[W_SQRTS], p[W_M], p[W_GAMMA], p[W_GF], p[W_VUD] = sqrt_s, M, Gamma, GF, Vud
+    p[W_PTMIN], p[W_ETAMAX], p[W_CUTS] = ptmin, etamax, cuts
+    p[W_SMIN] = (2.0 * ptmin) ** 2 if smin is None else smin
+    p[W_AU], p[W_ALU], p[W_BU] = u_pdf
+    p[W_AD], p[W_ALD], p[W_BD] = dbar_pdf
+    return p
+
+
+# The two-peak Gaussian as a user integrand.  Its parameter vector holds the
+# constants the source reads: p = (c1, c2, 1/w^2, (w sqrt(pi))^-d / 2).
+DGAUSS_USER_SOURCE = r"""
+template <typename T>
+__device__ T vegas_user_f(const T* x, int d, const T* p) {
+  T q1 = T(0), q2 = T(0);
+  for (int i = 0; i < d; ++i) {
+    const T t1 = x[i] - p[0], t2 = x[i] - p[1];
+    q1 += t1 * t1;
+    q2 += t2 * t2;
+  }
+  return p[3] * (gv::gexp(-q1 * p[2]) + gv::gexp(-q2 * p[2]));
+}
+"""
+
+
+def double_gaussian_user_params(d: int = 8, c1: float = 1.0 / 3.0, c2: float = 2.0 / 3.0,
+                                w: float = 0.05) -> np.ndarray:
+    return np.array([c1, c2, 1.0 / (w * w), 0.5 * (w * math.sqrt(math.pi)) ** (-d)], dtype=np.float64)
 
 
 def rambo_params(n: int, sqrt_s: float = 1000.0, M: float = 80.4,
@@ -83,6 +132,11 @@ WORKLOADS = {
     "rambo4_adjoint": dict(kind=RAMBO_BW, ndim=16, params=rambo_params(4, cut=1),
                            nbins=50, ncall=1 << 24, warmup_iters=5, nstrat=0,
                            seed=1, precision="fp32", ybits=24, mode="adjoint"),
+    # dgauss8 with the integrand compiled at run time from DGAUSS_USER_SOURCE
+    "user_dgauss8": dict(kind=USER, source=DGAUSS_USER_SOURCE, ndim=8, params=double_gaussian_user_params(8),
+                         oracle_kind=DOUBLE_GAUSSIAN, oracle_params=double_gaussian_params(),
+                         nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,
+                         precision="fp32", ybits=24, mode="bases"),
     # SPRING on the dgauss8 BASES run: 2^24 trials per step on its frozen grid
     "spring_dgauss8": dict(kind=DOUBLE_GAUSSIAN, ndim=8, params=double_gaussian_params(),
                            nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,

@@ -182,3 +182,19 @@ def test_zero_parameter_integrand(gv):
     with gv.vegas_create_user(src, 6, [], ncall=100003, precision=2) as ctx:
         r = gv.vegas_iterate(ctx, 3)
     assert abs(r["I"] - 3.0) <= 5 * r["sigma"]
+
+
+def test_user_dgauss8_workload_source_matches_the_oracle(gv, orc):
+    """The benchmarked user source (two-peak Gaussian, d = 8) at a reduced NCALL
+    (65 536 cubes x 2 points) against the oracle's built-in twin."""
+    w = wl.WORKLOADS["user_dgauss8"]
+    d, g, N = w["ndim"], w["nstrat"], w["nbins"]
+    ncall = g ** d * 2
+    with gv.vegas_create_user(w["source"], d, w["params"], nbins=N, ncall=ncall, nstrat=g, precision=2,
+                              ybits=24) as ctx:
+        I, var = gv.vegas_eval(ctx, 1)
+    cfg = orc.make_cfg(d, nbins=N, ncall=ncall, nstrat=g, ybits=24)
+    o = orc.iteration(cfg, orc.Integrand(w["oracle_kind"], d, w["oracle_params"]), orc.uniform_grid(d, N), 1)
+    sig = math.sqrt(o["var"])
+    assert abs(I - o["I"]) <= 1e-5 * abs(o["I"]) and abs(I - o["I"]) <= 0.1 * sig
+    assert abs(math.sqrt(var) - sig) <= 1e-3 * sig
