@@ -41,6 +41,10 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # work; the peak is the FP32 issue rate of all SMs at the maximum clock).
 ALGO_OPS = {
     "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, accumulate=8 * 2 + 2 + 12),
+    # the W integrand counted for the points of the coupling helicity cell
+    # (the adapted grid sends nearly all points there): tan, three logs,
+    # two exponentials for x1 and x2, the eta cut, the density exponent
+    "wmunu": dict(philox=2 * 10 * 6, bins=5 * 8, map=5 * 3, integrand=90, accumulate=5 * 2 + 2 + 12),
     "user_dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8,
                          accumulate=8 * 2 + 2 + 12),
     "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),
@@ -56,7 +60,7 @@ ALGO_OPS = {
 }
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/); None until captured for the current kernel.
-TRAFFIC = {"dgauss8": 68096}
+TRAFFIC = {"dgauss8": 68096, "wmunu": 66560}
 
 
 def _workload(name):
@@ -320,6 +324,7 @@ def _config(name):
     w = _workload(name)
     c = {"workload": name, "ndim": w["ndim"], "nbins": w["nbins"], "ncall": w["ncall"],
          "integrand": {0: "genz_gaussian", 4: "double_gaussian", 5: "rambo_bw",
+                       8: "u dbar -> W+ -> mu+ nu (stand-in densities)",
                        64: "double_gaussian as run-time compiled CUDA source"}[w["kind"]],
          "precision": w["precision"], "ybits": w["ybits"], "nstrat": w["nstrat"],
          "l2": "flushed between steps (512 MiB write)"}
@@ -702,7 +707,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dgauss8",
                     choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256", "spring_dgauss8",
-                             "user_dgauss8"])
+                             "user_dgauss8", "wmunu"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

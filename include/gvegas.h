@@ -82,7 +82,19 @@ typedef enum {
  *      V_n = (pi/2)^(n-1) s^(n-2) / ((n-1)!(n-2)!), cut = hard pT > ptmin
  *      or prod_i sigmoid((pT_i - T)/wc), and Delta R_ij > drmin for all
  *      pairs.  Units GeV.  (Stand-in for the W + n-gluon processes of
- *      Sec. 4, eq. 1, with the jet cuts of eqs. 2-3.) */
+ *      Sec. 4, eq. 1, with the jet cuts of eqs. 2-3.)
+ *  VG_W_MUNU             15 slots (VG_W_*), d = 5:  u dbar -> W+ -> mu+ nu_mu
+ *      in pp collisions (Sec. 4, the process with n = 0 gluons, and the mu+
+ *      cuts |eta| < ETAMAX, pT > PTMIN), f in pb.  y1 -> shat = M^2 +
+ *      M Gamma tan(rho), rho uniform between the images of [SMIN, S];
+ *      y2 -> W rapidity uniform in [ln(tau)/2, -ln(tau)/2]; y3 -> cos theta
+ *      of the mu+ against the u (which comes from the proton along +z) in
+ *      the partonic frame; y4 -> its azimuth; y5 -> one of 16 helicity
+ *      combinations, weight 16 (Sec. 4: one variable sums the helicities).
+ *      |M|^2 = g^4 |V_ud|^2 uhat^2 / ((shat - M^2)^2 + M^2 Gamma^2) for
+ *      u(-) dbar(+) -> nu(-) mu+(+), zero for the others, averaged over
+ *      spins and colours (1/12); g^2 = 8 M^2 G_F / sqrt 2.  Parton densities
+ *      A x^a (1 - x)^b per flavour (a stand-in for a PDF table). */
 typedef enum {
   VG_GENZ_GAUSSIAN = 0,
   VG_GENZ_PRODUCT_PEAK = 1,
@@ -92,9 +104,20 @@ typedef enum {
   VG_RAMBO_BW = 5,
   VG_GENZ_CONTINUOUS = 6,
   VG_GENZ_DISCONTINUOUS = 7,
+  VG_W_MUNU = 8,
   VG_USER = 64          /* run-time compiled (vegas_create_user); not valid
                            for vegas_create or the batched and no-alloc calls */
 } vegas_integrand_kind;
+
+enum {
+  VG_W_SQRTS = 0, VG_W_M = 1, VG_W_GAMMA = 2, VG_W_GF = 3, VG_W_VUD = 4,
+  VG_W_PTMIN = 5, VG_W_ETAMAX = 6,
+  VG_W_SMIN = 7,   /* lower end of the shat range, GeV^2                  */
+  VG_W_CUTS = 8,   /* 1: apply the mu+ cuts, 0: none                      */
+  VG_W_AU = 9, VG_W_ALU = 10, VG_W_BU = 11,   /* u density A, a, b         */
+  VG_W_AD = 12, VG_W_ALD = 13, VG_W_BD = 14,  /* dbar density A, a, b      */
+  VG_W_NPARAMS = 15
+};
 
 enum {
   VG_RB_N = 0, VG_RB_SQRTS = 1, VG_RB_M = 2, VG_RB_GAMMA = 3,
@@ -347,7 +370,7 @@ vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
  * instance), a whole call captured in one CUDA graph.
  *
  * Instances share precision (VG_FP64 or VG_FP32_ACCCOMP), ybits, nbins and
- * seed; each has its own integrand (any kind but VG_RAMBO_BW), ndim
+ * seed; each has its own integrand (any kind but VG_RAMBO_BW and VG_W_MUNU), ndim
  * (1..16), ncall (< 2^32), alpha and `instance` id (Philox counter word 3,
  * so instance i draws the points a standalone context with the same id
  * draws).  No stratification and no ACC stop.  The stream of cfgs[0] (or a

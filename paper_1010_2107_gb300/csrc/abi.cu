@@ -148,6 +148,8 @@ bool lookup_kernel(int kind, int prec, int ybits, int d, gv::KernelEntry* e) {
       return y24 ? gv::entries_dgauss_y24(prec, d, e) : gv::entries_dgauss_y53(prec, d, e);
     case VG_RAMBO_BW:
       return y24 ? gv::entries_rambo_y24(prec, d, e) : gv::entries_rambo_y53(prec, d, e);
+    case VG_W_MUNU:
+      return y24 ? gv::entries_wmunu_y24(prec, d, e) : gv::entries_wmunu_y53(prec, d, e);
     case VG_GENZ_CONTINUOUS:
       return y24 ? gv::entries_genz_continuous_y24(prec, d, e) : gv::entries_genz_continuous_y53(prec, d, e);
     case VG_GENZ_DISCONTINUOUS:

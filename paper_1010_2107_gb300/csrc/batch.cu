@@ -640,7 +640,8 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
     if (c.ncall < 2 || c.ncall > ((int64_t)1 << 32) - 1) return bfail("ncall outside 2..2^32-1");
     if (!(c.alpha >= 0.0)) return bfail("alpha must be >= 0");
     if (fns[i].ndim != c.ndim) return bfail("integrand ndim differs from config ndim");
-    if (fns[i].kind == VG_RAMBO_BW) return bfail("RAMBO integrands are not batched");
+    if (fns[i].kind == VG_RAMBO_BW || fns[i].kind == VG_W_MUNU)
+      return bfail("RAMBO and W -> mu nu integrands are not batched");
     const int np = gv::expected_nparams(fns[i].kind, c.ndim);
     if (np < 0 || fns[i].nparams != np || (np > 0 && !fns[i].params))
       return bfail("integrand parameter count does not match its kind");

@@ -197,31 +197,13 @@ struct DoubleGaussian {
   static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
     const T c1 = P[kScalar], c2 = P[kScalar + 1];
     T q1 = T(0), q2 = T(0);
-    if constexpr (std::is_same<T, float>::value && DM % 2 == 0) {
-      // two axes per paired FP32 instruction (FADD2 / FFMA2); an axis past
-      // d contributes nothing
-      float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-      const float2 m1 = make_float2(-c1, -c1), m2 = make_float2(-c2, -c2);
 #pragma unroll
-      for (int a = 0; a < DM; a += 2)
-        if (a < d) {
-          const float2 xa = make_float2(x[a], a + 1 < d ? x[a + 1] : c1);
-          const float2 xb = make_float2(x[a], a + 1 < d ? x[a + 1] : c2);
-          const float2 t1 = __fadd2_rn(xa, m1), t2 = __fadd2_rn(xb, m2);
-          s1 = __ffma2_rn(t1, t1, s1);
-          s2 = __ffma2_rn(t2, t2, s2);
-        }
-      q1 = s1.x + s1.y;
-      q2 = s2.x + s2.y;
-    } else {
-#pragma unroll
-      for (int a = 0; a < DM; ++a)
-        if (a < d) {
-          const T t1 = x[a] - c1, t2 = x[a] - c2;
-          q1 = vfma(t1, t1, q1);
-          q2 = vfma(t2, t2, q2);
-        }
-    }
+    for (int a = 0; a < DM; ++a)
+      if (a < d) {
+        const T t1 = x[a] - c1, t2 = x[a] - c2;
+        q1 = vfma(t1, t1, q1);
+        q2 = vfma(t2, t2, q2);
+      }
     const T iw2 = P[kScalar + 2];
     return P[kScalar + 3] * (gexp(-q1 * iw2) + gexp(-q2 * iw2));
   }
@@ -458,6 +440,51 @@ struct RamboBW {
     const T f = pre * b;
     g[2] = f * dlc;
     return f;
+  }
+};
+
+// --------------------------------------------------- u dbar -> W+ -> mu+ nu
+// Sec. 4's process with n = 0 gluons and the mu+ cuts, five variables
+// (Breit-Wigner shat, W rapidity, cos theta and azimuth of the mu+, the
+// helicity combination; the slot layout of VG_W_MUNU in gvegas.h).  Only
+// u(-) dbar(+) -> nu(-) mu+(+) couples, so the other 15 helicity cells
+// return 0 at once.  With shat = M^2 + M Gamma tan(rho) the Breit-Wigner
+// denominator cancels against dshat/drho = M Gamma sec^2(rho), and the
+// product of flux, phase space, averaged |M|^2 and Jacobians reduces to
+//   f = K exp(a_u ln x1 + b_u ln(1 - x1) + a_d ln x2 + b_d ln(1 - x2)) L shat (1 - c)^2
+// with L = -ln tau, ln x1,2 = -L/2 +- y_W, c = cos theta, and
+// K = A_u A_d Delta rho g^4 |V_ud|^2 (pb GeV^2) / (48 pi S M Gamma).
+enum {
+  W_RLO = kScalar, W_DRHO, W_M2, W_MG, W_INVS, W_PT2, W_ETA, W_CUTS, W_K, W_ALU, W_BU, W_ALD, W_BD
+};
+constexpr int kWHelicity = 0 | 2 | 0 | 8;  // bits u, dbar, nu, mu+ (1 = positive)
+
+template <typename T, int DM>
+struct WMuNu {
+  static __device__ __forceinline__ T eval(const T (&x)[DM], int d, const T* P) {
+    const int h = (int)(x[4] * T(16));  // x < 1: the cell floor(16 y5)
+    if ((h < 15 ? h : 15) != kWHelicity) return T(0);
+    T sn, cs;
+    const T rho = vfma(P[W_DRHO], x[0], P[W_RLO]);
+    if constexpr (std::is_same<T, float>::value)
+      __sincosf(rho, &sn, &cs);
+    else
+      sincos(rho, &sn, &cs);
+    const T shat = vfma(P[W_MG], qdiv(sn, cs), P[W_M2]);
+    const T L = -qlog_rel(shat * P[W_INVS]);
+    const T yw = (x[1] - T(0.5)) * L;
+    const T lx1 = vfma(T(-0.5), L, yw), lx2 = vfma(T(-0.5), L, -yw);
+    const T x1 = qexp(lx1), x2 = qexp(lx2);
+    if (!(x1 < T(1) && x2 < T(1) && L > T(0))) return T(0);
+    const T c = vfma(T(2), x[2], T(-1));
+    if (P[W_CUTS] != T(0)) {
+      if (!(shat * (T(1) - c) * (T(1) + c) > P[W_PT2])) return T(0);
+      const T eta = vfma(T(0.5), qlog(qdiv(T(1) + c, T(1) - c)), yw);
+      if (!(fabs(eta) < P[W_ETA])) return T(0);
+    }
+    const T e = P[W_ALU] * lx1 + P[W_BU] * qlog_rel(T(1) - x1) + P[W_ALD] * lx2 + P[W_BD] * qlog_rel(T(1) - x2);
+    const T omc = T(1) - c;
+    return P[W_K] * qexp(e) * L * shat * omc * omc;
   }
 };
 

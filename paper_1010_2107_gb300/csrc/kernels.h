@@ -51,6 +51,8 @@ bool entries_genz_continuous_y24(int prec, int d, KernelEntry* out);
 bool entries_genz_continuous_y53(int prec, int d, KernelEntry* out);
 bool entries_genz_discontinuous_y24(int prec, int d, KernelEntry* out);
 bool entries_genz_discontinuous_y53(int prec, int d, KernelEntry* out);
+bool entries_wmunu_y24(int prec, int d, KernelEntry* out);
+bool entries_wmunu_y53(int prec, int d, KernelEntry* out);
 bool entries_rambo_y24(int prec, int d, KernelEntry* out);
 bool entries_rambo_y53(int prec, int d, KernelEntry* out);
 

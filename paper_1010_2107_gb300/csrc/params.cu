@@ -20,6 +20,7 @@ int expected_nparams(int kind, int d) {
     case VG_RAMBO_BW: return VG_RB_NPARAMS;
     case VG_GENZ_CONTINUOUS: return 2 * d;
     case VG_GENZ_DISCONTINUOUS: return d + (d < 2 ? d : 2);
+    case VG_W_MUNU: return VG_W_NPARAMS;
     default: return -1;
   }
 }
@@ -119,6 +120,40 @@ bool derive_params(int kind, int d, const double* p, double* dv, double* scale, 
         case 2: *scale = V * s; break;
         default: *scale = V / s; break;
       }
+      return true;
+    }
+    case VG_W_MUNU: {
+      if (d != 5) {
+        *why = "the W -> mu nu integrand has ndim 5";
+        return false;
+      }
+      const double rs = p[VG_W_SQRTS], S = rs * rs, Mw = p[VG_W_M], Gw = p[VG_W_GAMMA];
+      if (!(rs > 0.0 && Mw > 0.0 && Gw > 0.0 && p[VG_W_SMIN] >= 0.0 && p[VG_W_SMIN] < S)) {
+        *why = "W -> mu nu needs sqrt(S), M, Gamma > 0 and 0 <= SMIN < S";
+        return false;
+      }
+      if (p[VG_W_CUTS] != 0.0 && p[VG_W_CUTS] != 1.0) {
+        *why = "W -> mu nu CUTS must be 0 or 1";
+        return false;
+      }
+      const double rlo = std::atan((p[VG_W_SMIN] - Mw * Mw) / (Mw * Gw));
+      const double rhi = std::atan((S - Mw * Mw) / (Mw * Gw));
+      const double g2 = 8.0 * Mw * Mw * p[VG_W_GF] / std::sqrt(2.0);
+      const double pb = 0.3893793721e9;  // GeV^-2 -> pb
+      dv[W_RLO] = rlo;
+      dv[W_DRHO] = rhi - rlo;
+      dv[W_M2] = Mw * Mw;
+      dv[W_MG] = Mw * Gw;
+      dv[W_INVS] = 1.0 / S;
+      dv[W_PT2] = 4.0 * p[VG_W_PTMIN] * p[VG_W_PTMIN];
+      dv[W_ETA] = p[VG_W_ETAMAX];
+      dv[W_CUTS] = p[VG_W_CUTS];
+      dv[W_K] = p[VG_W_AU] * p[VG_W_AD] * (rhi - rlo) * g2 * g2 * p[VG_W_VUD] * p[VG_W_VUD] * pb /
+                (48.0 * M_PI * S * Mw * Gw);
+      dv[W_ALU] = p[VG_W_ALU];
+      dv[W_BU] = p[VG_W_BU];
+      dv[W_ALD] = p[VG_W_ALD];
+      dv[W_BD] = p[VG_W_BD];
       return true;
     }
     default:

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgvegas.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE, ESTATE = range(7)
 # vegas_integrand_kind
 (GENZ_GAUSSIAN, GENZ_PRODUCT_PEAK, GENZ_CORNER_PEAK, GENZ_OSCILLATORY, DOUBLE_GAUSSIAN, RAMBO_BW,
- GENZ_CONTINUOUS, GENZ_DISCONTINUOUS) = range(8)
+ GENZ_CONTINUOUS, GENZ_DISCONTINUOUS, W_MUNU) = range(9)
 USER = 64  # run-time compiled integrand (vegas_create_user)
 MAXUSERPARAMS = 120
 # vegas_precision

@@ -21,6 +21,9 @@ iterations, BASES split ITMX1 = ITMX2 with ITMX1 + ITMX2 = ITMX):
                5-iteration grid warm-up.
 * ``user_dgauss8``  ``dgauss8`` with the integrand given as CUDA source
                (``DGAUSS_USER_SOURCE``) and compiled at run time.
+* ``wmunu``    BASES, hypercube-stratified (8 divisions per axis, 32 768 cubes
+               x 128 points), FP32, u dbar -> W+ -> mu+ nu at sqrt(S) = 14 TeV
+               with the mu+ cuts (5 dims), 32 bins, 5 + 5 iterations x 2^22.
 * ``genz256``  256 Genz integrands (product peak, corner peak, oscillatory),
                d uniform in 2..16, points per instance log-uniform in
                2^16..2^22, 8 iterations each.
@@ -137,6 +140,9 @@ WORKLOADS = {
                          oracle_kind=DOUBLE_GAUSSIAN, oracle_params=double_gaussian_params(),
                          nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,
                          precision="fp32", ybits=24, mode="bases"),
+    # the physics workload of Sec. 4 with n = 0 gluons (stand-in densities)
+    "wmunu": dict(kind=W_MUNU, ndim=5, params=w_munu_params(), nbins=32, ncall=1 << 22, itmx1=5, itmx2=5,
+                  nstrat=8, seed=1, precision="fp32", ybits=24, mode="bases"),
     # SPRING on the dgauss8 BASES run: 2^24 trials per step on its frozen grid
     "spring_dgauss8": dict(kind=DOUBLE_GAUSSIAN, ndim=8, params=double_gaussian_params(),
                            nbins=50, ncall=1 << 22, itmx1=5, itmx2=5, nstrat=4, seed=1,

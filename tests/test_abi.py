@@ -65,6 +65,7 @@ def test_invalid_config_is_rejected(gvlib, bad, msg):
 
 @pytest.mark.parametrize("kind,ndim,np_,msg", [
     (0, 4, 7, "parameters"), (5, 20, 10, None), (5, 18, 10, "4 n"), (9, 4, 4, "kind"),
+    (8, 4, 15, "ndim 5"), (8, 5, 14, "parameters"), (8, 5, 15, "CUTS"), (8, 5, 15, "SMIN"),
 ])
 def test_invalid_integrand_is_rejected(gvlib, kind, ndim, np_, msg):
     gv = gvlib
@@ -75,6 +76,12 @@ def test_invalid_integrand_is_rejected(gvlib, kind, ndim, np_, msg):
         p = p.copy()
         p[wl.RB_CUT] = 7
         msg = "cut"
+    if kind == 8 and np_ == 15:
+        p = wl.w_munu_params()
+        if msg == "CUTS":
+            p[wl.W_CUTS] = 2
+        if msg == "SMIN":
+            p[wl.W_SMIN] = p[wl.W_SQRTS] ** 2
     cfg = _cfg(gv, ndim=ndim)
     fn = gv.IntegrandDesc(kind, ndim, p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(p))
     h = ctypes.c_void_p()

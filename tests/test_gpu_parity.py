@@ -46,6 +46,8 @@ CASES = [
     ("gauss3strat3", wl.GENZ_GAUSSIAN, 3, wl.genz_gaussian_params(3, a=5.0), dict(nstrat=3, ncall=27 * 37)),
     ("cont4", wl.GENZ_CONTINUOUS, 4, np.array([3.0, 5.0, 2.0, 4.0, 0.3, 0.6, 0.5, 0.45]), {}),
     ("disc3", wl.GENZ_DISCONTINUOUS, 3, np.array([1.5, 2.0, 0.7, 0.4, 0.6]), {}),
+    ("wmunu", wl.W_MUNU, 5, wl.w_munu_params(), {}),
+    ("wmunu_strat", wl.W_MUNU, 5, wl.w_munu_params(), dict(nstrat=4, ncall=4 ** 5 * 12)),
 ]
 
 
@@ -74,7 +76,7 @@ def test_words_bins_points(gv, orc, name, kind, d, params, kw, precision, ybits)
                 ok = np.isclose(fg, fo, rtol=2e-4, atol=1e-300 + 1e-6 * np.max(np.abs(fo)))
             # cut decisions (and the discontinuous family's edges) may flip for
             # points within rounding of the edge
-            flips = kind in (wl.RAMBO_BW, wl.GENZ_DISCONTINUOUS)
+            flips = kind in (wl.RAMBO_BW, wl.GENZ_DISCONTINUOUS, wl.W_MUNU)
             assert np.mean(ok) >= (0.99 if flips else 1.0), np.flatnonzero(~ok)[:10]
 
 
@@ -306,3 +308,21 @@ def test_set_launch_limits(gv):
     with ctx:  # general kernel (d below the compiled bound): 256 at most
         with pytest.raises(gv.VegasError):
             gv.vegas_set_launch(ctx, 384)
+
+
+def test_bases_wmunu_fp64_matches_the_oracle(gv, orc):
+    """The W workload's BASES run (both phases, refinement between the first
+    phase's iterations) at a reduced NCALL, FP64, against the oracle."""
+    d, g, N = 5, 4, 50
+    ncall = g ** d * 24
+    p = wl.w_munu_params()
+    with gv.vegas_create(wl.W_MUNU, d, p, nbins=N, ncall=ncall, nstrat=g, precision=0, ybits=24) as ctx:
+        r, ph1 = gv.bases_integrate(ctx, 3, 0.0, 2, 0.0)
+        edges = gv.vegas_get_grid(ctx)
+    cfg = orc.make_cfg(d, nbins=N, ncall=ncall, nstrat=g, ybits=24)
+    e = orc.uniform_grid(d, N)
+    ref = orc.bases(cfg, orc.Integrand(wl.W_MUNU, d, p), e, 0, 3, 0.0, 2, 0.0)
+    assert (ph1["iters_done"], r["iters_done"]) == (3, 2)
+    assert abs(r["I"] - ref["I"]) <= 1e-11 * abs(ref["I"])
+    assert abs(r["sigma"] - ref["sigma"]) <= 1e-9 * ref["sigma"]
+    assert np.max(np.abs(edges - e)) < 1e-11

@@ -51,7 +51,8 @@ def test_cube_maxima_match_the_oracle(gv, orc, precision):
     (wl.GENZ_PRODUCT_PEAK, 2, np.array([5.0, 3.0, 0.3, 0.6])),
     (wl.DOUBLE_GAUSSIAN, 4, wl.double_gaussian_params(w=0.15)),
     (wl.GENZ_GAUSSIAN, 3, wl.genz_gaussian_params(3, a=4.0)),
-], ids=["pp2", "dg4", "gauss3"])
+    (wl.W_MUNU, 5, wl.w_munu_params()),
+], ids=["pp2", "dg4", "gauss3", "wmunu"])
 def test_spring_fp64_matches_the_oracle(gv, orc, kind, d, params):
     ctx, cfg, fn, edges, cmax, ref = _run(gv, orc, kind, d, params, 0)
     with ctx:
