@@ -216,7 +216,11 @@ vegas_status bases_integrate(vegas_ctx* ctx, int itmx1, double acc1,
                              vegas_result* phase1);
 
 /* Copy the grid edges [ndim][nbins+1] and, if bin_sums is not NULL, the
- * per-bin sums of the last iteration [2][ndim][nbins] (sum w, sum w^2). */
+ * per-bin sums [2][ndim][nbins] (sum w, sum w^2) of the last pass that
+ * formed them: a refining iteration or vegas_eval.  Passes that leave the
+ * grid unchanged (vegas_iterate with refine = 0, the integration phase of
+ * bases_integrate) skip them, since only the grid optimisation (step 5)
+ * reads them; their estimates, cube sums and maxima are complete. */
 vegas_status vegas_get_grid(vegas_ctx* ctx, double* edges, double* bin_sums);
 
 /* Replace the grid (resume / freeze).  Edges must start at 0, end at 1 and

@@ -62,6 +62,8 @@ struct vegas_ctx {
   // launch geometry
   int threads = 256, ctas_per_sm_req = 0, ctas = 0, lanes = 1, lanes_req = 0, occ = 0;
   int cap = 16;  // histogram bucket capacity (see sample_kernel.cuh)
+  int ctas_nb = 0;      // CTAs of a pass without the per-bin histogram
+  size_t smem_nb = 0;   // and its dynamic shared memory
   int ppt = 1, ppt_req = 0, ppt_min = 1;  // points per thread per histogram tile
   size_t smem = 0;
   // device buffers
@@ -285,22 +287,33 @@ vegas_status configure_launch(vegas_ctx* c) {
   }
   int64_t ctas = (int64_t)((units + c->threads - 1) / c->threads);
   c->ctas = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, cap_ctas));
-  if (c->ctas > c->part_rows) {
+  // passes without the per-bin histogram (no refinement) need only the
+  // grid table and constants in shared memory: more CTAs may be resident
+  c->smem_nb = c->ke.smem_nobins(d, N);
+  int occ_nb = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_nb, c->ke.sample, c->threads, c->smem_nb);
+  if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
+  occ_nb = std::max(occ_nb, per_sm);
+  if (c->ctas_per_sm_req > 0) occ_nb = std::min(occ_nb, std::max(c->ctas_per_sm_req, per_sm));
+  c->ctas_nb = (int)std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)c->sm_count * occ_nb));
+  const int rows = std::max(c->ctas, c->ctas_nb);
+  if (rows > c->part_rows) {
     if (c->d_part_bins) cudaFree(c->d_part_bins);
     if (c->d_part_tot) cudaFree(c->d_part_tot);
     c->d_part_bins = nullptr;
     c->d_part_tot = nullptr;
     c->part_rows = 0;
-    CK(c, cudaMalloc(&c->d_part_bins, sizeof(double) * 2 * (size_t)d * N * c->ctas));
-    CK(c, cudaMalloc(&c->d_part_tot, sizeof(double) * gv::kTotCols * (size_t)c->ctas));
-    c->part_rows = c->ctas;
+    CK(c, cudaMalloc(&c->d_part_bins, sizeof(double) * 2 * (size_t)d * N * rows));
+    CK(c, cudaMalloc(&c->d_part_tot, sizeof(double) * gv::kTotCols * (size_t)rows));
+    c->part_rows = rows;
   }
   destroy_graphs(c);
   return VEGAS_OK;
 }
 
-gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
+gv::SampleArgs sample_args(const vegas_ctx* c, int it_override, bool nobins = false) {
   gv::SampleArgs A{};
+  A.nobins = nobins;
   A.d = c->cfg.ndim;
   A.N = c->cfg.nbins;
   A.g = c->g;
@@ -328,7 +341,7 @@ gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
   A.inv_gb_f = (float)(1.0 / gb);
   A.inv_nc = c->nc > 0 ? 1.0 / (double)c->nc : 0.0;
   A.inv_nc1 = c->nc > 1 ? 1.0 / (double)(c->nc - 1) : 0.0;
-  A.nparts = c->ctas;
+  A.nparts = nobins ? c->ctas_nb : c->ctas;
   A.tab = c->prec == VG_FP64 ? (const void*)c->d_tab64 : (const void*)c->d_tab32;
   A.dparams = c->d_derived;
   A.st = c->d_st;
@@ -338,11 +351,12 @@ gv::SampleArgs sample_args(const vegas_ctx* c, int it_override) {
   return A;
 }
 
-gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record) {
+gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record, bool nobins = false) {
   gv::FinArgs F{};
   F.d = c->cfg.ndim;
   F.N = c->cfg.nbins;
-  F.nparts = c->ctas;
+  F.nobins = nobins;
+  F.nparts = nobins ? c->ctas_nb : c->ctas;
   F.strat = c->strat;
   F.refine = refine;
   F.record = record;
@@ -362,13 +376,18 @@ gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record) {
   return F;
 }
 
-// One pass of steps 2-6 on the context stream.
-vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record, bool record_max = false) {
-  gv::SampleArgs A = sample_args(c, it_override);
+// One pass of steps 2-6 on the context stream.  A pass that does not
+// refine the grid skips the per-bin histogram, whose sums only step 5
+// reads (`nobins`), unless the caller wants them.
+vegas_status launch_pass(vegas_ctx* c, int it_override, int refine, int record, bool record_max = false,
+                         bool nobins = false) {
+  if (refine) nobins = false;
+  gv::SampleArgs A = sample_args(c, it_override, nobins);
   if (record_max) A.cube_max = c->d_cube_max;
   void* args[] = {&A};
-  CK(c, cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream));
-  gv::FinArgs F = fin_args(c, refine, record);
+  CK(c, cudaLaunchKernel(c->ke.sample, dim3(nobins ? c->ctas_nb : c->ctas), dim3(c->threads), args,
+                         nobins ? c->smem_nb : c->smem, c->stream));
+  gv::FinArgs F = fin_args(c, refine, record, nobins);
   CK(c, gv_launch_finish(&F, c->stream));
   return VEGAS_OK;
 }
@@ -395,7 +414,7 @@ vegas_status get_graph(vegas_ctx* c, int shape, int n1, int n2, int refine, doub
   };
   if (shape == 0) {
     ctl(gv::CTL_SET_ACC, acc1);
-    for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, refine, 1);
+    for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, refine, 1, false, !refine);
   } else {
     ctl(gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, acc1);
     for (int i = 0; i < n1 && !st; ++i) st = launch_pass(c, -1, 1, 1);
@@ -403,7 +422,7 @@ vegas_status get_graph(vegas_ctx* c, int shape, int n1, int n2, int refine, doub
     // the integration phase records the per-cube maxima that SPRING uses
     if (!st && cudaMemsetAsync(c->d_cube_max, 0, sizeof(double) * c->ncubes, c->stream) != cudaSuccess)
       st = c->fail(VEGAS_ECUDA, "cube maxima reset");
-    for (int i = 0; i < n2 && !st; ++i) st = launch_pass(c, -1, 0, 1, true);
+    for (int i = 0; i < n2 && !st; ++i) st = launch_pass(c, -1, 0, 1, true, true);
   }
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (st != VEGAS_OK) {

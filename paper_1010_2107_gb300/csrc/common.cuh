@@ -180,6 +180,11 @@ __device__ __forceinline__ void qsincos2pi(float u, float* s, float* c) {
 }
 __device__ __forceinline__ void qsincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
 
+// A compile-time flag as a type (selects a code path of a generic lambda).
+template <bool V> struct BoolTag {
+  static constexpr bool value = V;
+};
+
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
@@ -220,6 +225,7 @@ struct SampleArgs {
   int cap;                 // bucket capacity per (axis, bin) and tile
   int ppt;                 // points per thread per tile (>= 1)
   int strat;
+  int nobins;              // 1: no per-bin histogram (a pass whose grid is not refined)
   uint32_t key0, key1, instance;
   uint32_t ks[kPhiloxKeyWords];  // Philox round keys of (key0, key1)
   int it_override;         // >= 0: use this iteration index
@@ -246,6 +252,7 @@ struct SampleArgs {
 // Arguments of the reduction and finalisation kernels (steps 4-6).
 struct FinArgs {
   int d, N, nparts, strat, refine, record;
+  int nobins;              // the pass kept no per-bin histogram: totals only, no refinement
   int pair32;              // part_bins hold float (hi, lo) pairs
   uint64_t ncall;
   uint64_t ncubes;

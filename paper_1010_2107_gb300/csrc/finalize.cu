@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(const FinArgs F) {
   const int N = F.N, dN = F.d * N;
   const int bpa = (2 * N + wpb - 1) / wpb;  // blocks per axis
   const int b = blockIdx.x;
-  const int group = b < F.d * bpa ? b / bpa : F.d;
+  // without per-bin sums only the totals block is launched
+  const int group = (!F.nobins && b < F.d * bpa) ? b / bpa : F.d;
   if (group < F.d) {
     const int a = group, i = (b - a * bpa) * wpb + warp;  // column of the axis, 0 .. 2N
     if (i < 2 * N) {
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(const FinArgs F) {
   if (!last) return;
   __threadfence();
   if (group < F.d) {
-    if (F.refine) refine_axis(F, group);
+    if (F.refine && !F.nobins) refine_axis(F, group);
   } else if (threadIdx.x < 32) {
     record_iteration(F);
   }
@@ -251,7 +252,7 @@ cudaError_t gv_prepare_aux_kernels(void) {
 
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s) {
   const int wpb = gv::kFinishThreads / 32;
-  const int blocks = F->d * ((2 * F->N + wpb - 1) / wpb) + 1;
+  const int blocks = F->nobins ? 1 : F->d * ((2 * F->N + wpb - 1) / wpb) + 1;
   gv::k_finish<<<blocks, gv::kFinishThreads, 0, s>>>(*F);
   return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ struct KernelEntry {
   const void* dump;                   // k_dump<T, DM, F>
   size_t (*smem)(int d, int N, int cap);  // dynamic shared memory of `sample`
                                           // with bucket capacity cap
+  size_t (*smem_nobins)(int d, int N);    // ... of a pass without the histogram
   int dm;                             // compile-time dimension bound
   int spec_ppt_min;                   // `sample_spec` evaluates this many points per
                                       // thread at a time: tiles are multiples of it

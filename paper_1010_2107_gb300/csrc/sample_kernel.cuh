@@ -393,8 +393,14 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
-  hist.zero_buckets(tid, blockDim.x, dN);
-  hist.zero(tid, blockDim.x);
+  // Per-bin sums feed only the grid refinement (step 5); a pass that does
+  // not refine (the integration phase of BASES, a frozen-grid VEGAS call)
+  // keeps its estimate, cube sums and maxima and skips the histogram.
+  const bool bins = !A.nobins;
+  if (bins) {
+    hist.zero_buckets(tid, blockDim.x, dN);
+    hist.zero(tid, blockDim.x);
+  }
   __syncthreads();
 
   int nonfinite = 0;
@@ -402,8 +408,6 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
 #pragma unroll
   for (int a = 0; a < DM; ++a) cd[a] = 0;
 
-  auto scatter = [&](const int (&kb)[DM], H w) { hist.template scatter<DM>(kb, d, w); };
-  auto gather = [&]() { hist.gather(tid, blockDim.x); };
   // w = f J in the kernel precision, widened to the histogram type H
   // (squares are then formed in H: FP64 unless ACC == 2).
   auto eval_point = [&](uint32_t s, int (&kb)[DM], bool valid = true) -> H {
@@ -427,123 +431,39 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
   // FP64 (ACC 0/1) or compensated FP32 pairs (ACC 2).
   double t[4] = {0.0, 0.0, 0.0, 0.0};
   fpair tp[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  if (!A.strat) {
-    Run<ACC> sw, sw2;
-    H pmax = H(0);  // largest weight (integration-phase maximum of the one cube)
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x;
-    const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
-    uint64_t s = first + tid;
-    int pend = 0;  // points per thread since the last gather (uniform in the CTA)
-    if constexpr (PAIR) {
-      for (uint64_t r = 0; r < rounds; r += 2, s += 2 * stride) {
-        const bool v0 = s < A.ncall, v1 = s + stride < A.ncall;
-        int kb0[DM], kb1[DM];
-        const H w0 = eval_point((uint32_t)s, kb0, v0);
-        const H w1 = eval_point((uint32_t)(s + stride), kb1, v1);
-        if (v0) {
-          sw.add(w0);
-          sw2.add(w0 * w0);
-          pmax = max(pmax, w0);
-          scatter(kb0, w0);
-        }
-        if (v1) {
-          sw.add(w1);
-          sw2.add(w1 * w1);
-          pmax = max(pmax, w1);
-          scatter(kb1, w1);
-        }
-        if ((pend += 2) >= A.ppt) {
-          gather();
-          pend = 0;
-        }
-      }
-    } else {
-      for (uint64_t r = 0; r < rounds; ++r, s += stride) {
-        if (s < A.ncall) {
-          int kb[DM];
-          const H w = eval_point((uint32_t)s, kb);
-          sw.add(w);
-          sw2.add(w * w);
-          pmax = max(pmax, w);
-          scatter(kb, w);
-        }
-        if (++pend == A.ppt) {
-          gather();
-          pend = 0;
-        }
-      }
-    }
-    if (pend) gather();
-    if (A.cube_max) {  // non-negative doubles order as their bit patterns
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off));
-      if (lane == 0 && pmax > H(0))
-        atomicMax(reinterpret_cast<unsigned long long*>(A.cube_max),
-                  (unsigned long long)__double_as_longlong((double)pmax));
-    }
-    if constexpr (COMP) {
-      tp[0] = sw.p;
-      tp[1] = sw2.p;
-    } else {
-      t[0] = sw.value();
-      t[1] = sw2.value();
-    }
-  } else {
-    // Groups of Lw lanes share a hypercube; lane j of a group takes the
-    // cube's points j, j + Lw, ... in lock-step with the rest of the CTA
-    // (one tile per step); the group then reduces its sums with a fixed
-    // xor-butterfly (deterministic).  Group i takes cube
-    // (i * cube_mul) mod ncubes, so that the groups of a CTA sit in
-    // unrelated cubes and spread over the bins.
-    const int Lw = A.lanes;
-    const int gl = tid & (Lw - 1);
-    const uint32_t groups_per_cta = blockDim.x / Lw;
-    const uint32_t gstride = gridDim.x * groups_per_cta;
-    const uint32_t gfirst = blockIdx.x * groups_per_cta;
-    const uint32_t rounds = gfirst < A.ncubes ? (A.ncubes - gfirst + gstride - 1) / gstride : 0;
-    const uint32_t cmask = A.ncubes - 1u;
-    const uint32_t per_lane = (A.nc + Lw - 1) / Lw;
-    uint32_t gi = gfirst + tid / Lw;
-    int pend = 0;  // points per thread since the last gather (uniform in the CTA)
-    for (uint32_t r = 0; r < rounds; ++r, gi += gstride) {
-      const bool live = gi < A.ncubes;  // uniform within a group
-      const uint32_t c = A.cube_mul == 1u ? gi : (gi * A.cube_mul) & cmask;
-      if (live) {
-        uint32_t rest = c;
-#pragma unroll
-        for (int a = 0; a < DM; ++a)
-          if (a < d) {
-            if (A.g_pow2) {
-              cd[a] = (int)(rest & (uint32_t)(A.g - 1));
-              rest >>= A.g_log2;
-            } else {
-              cd[a] = (int)(rest % (uint32_t)A.g);
-              rest /= (uint32_t)A.g;
-            }
-          }
-      }
-      const uint32_t s0 = c * A.nc;
-      // a lane's chain of points in one cube is short: plain sums in H,
-      // compensated merges across the group; pmax: the largest weight (for
-      // the per-cube maxima of the integration phase)
-      H p1 = H(0), p2 = H(0), pmax = H(0);
+  // The pass loop, compiled twice: with the per-bin histogram and without
+  // it (a uniform choice per launch; no test inside the loops).
+  auto pass = [&](auto with_bins) {
+    constexpr bool B = decltype(with_bins)::value;
+    auto scatter = [&](const int (&kb)[DM], H w) {
+      if constexpr (B) hist.template scatter<DM>(kb, d, w);
+    };
+    auto gather = [&]() {
+      if constexpr (B) hist.gather(tid, blockDim.x);
+    };
+    if (!A.strat) {
+      Run<ACC> sw, sw2;
+      H pmax = H(0);  // largest weight (integration-phase maximum of the one cube)
+      const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+      const uint64_t first = (uint64_t)blockIdx.x * blockDim.x;
+      const uint64_t rounds = first < A.ncall ? (A.ncall - first + stride - 1) / stride : 0;
+      uint64_t s = first + tid;
+      int pend = 0;  // points per thread since the last gather (uniform in the CTA)
       if constexpr (PAIR) {
-        for (uint32_t i = 0; i < per_lane; i += 2) {
-          const uint32_t j0 = gl + i * Lw, j1 = j0 + Lw;
-          const bool v0 = live && j0 < A.nc, v1 = live && j1 < A.nc;
+        for (uint64_t r = 0; r < rounds; r += 2, s += 2 * stride) {
+          const bool v0 = s < A.ncall, v1 = s + stride < A.ncall;
           int kb0[DM], kb1[DM];
-          const H w0 = eval_point(s0 + j0, kb0, v0);
-          const H w1 = eval_point(s0 + j1, kb1, v1);
+          const H w0 = eval_point((uint32_t)s, kb0, v0);
+          const H w1 = eval_point((uint32_t)(s + stride), kb1, v1);
           if (v0) {
-            p1 += w0;
-            p2 += w0 * w0;
+            sw.add(w0);
+            sw2.add(w0 * w0);
             pmax = max(pmax, w0);
             scatter(kb0, w0);
           }
           if (v1) {
-            p1 += w1;
-            p2 += w1 * w1;
+            sw.add(w1);
+            sw2.add(w1 * w1);
             pmax = max(pmax, w1);
             scatter(kb1, w1);
           }
@@ -553,13 +473,12 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
           }
         }
       } else {
-        for (uint32_t i = 0; i < per_lane; ++i) {
-          const uint32_t j = gl + i * Lw;
-          if (live && j < A.nc) {
+        for (uint64_t r = 0; r < rounds; ++r, s += stride) {
+          if (s < A.ncall) {
             int kb[DM];
-            const H w = eval_point(s0 + j, kb);
-            p1 += w;
-            p2 += w * w;
+            const H w = eval_point((uint32_t)s, kb);
+            sw.add(w);
+            sw2.add(w * w);
             pmax = max(pmax, w);
             scatter(kb, w);
           }
@@ -569,68 +488,168 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
           }
         }
       }
-      if (A.cube_max) {  // integration phase: per-cube maxima (one group per cube)
-        for (int off = Lw >> 1; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off, Lw));
-        if (live && gl == 0) A.cube_max[c] = fmax(A.cube_max[c], (double)pmax);
+      if (pend) gather();
+      if (A.cube_max) {  // non-negative doubles order as their bit patterns
+  #pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off));
+        if (lane == 0 && pmax > H(0))
+          atomicMax(reinterpret_cast<unsigned long long*>(A.cube_max),
+                    (unsigned long long)__double_as_longlong((double)pmax));
       }
       if constexpr (COMP) {
-        fpair c1{p1, 0.f}, c2{p2, 0.f};
-        for (int off = Lw >> 1; off > 0; off >>= 1) {
-          fpair o1, o2;
-          o1.hi = __shfl_xor_sync(0xffffffffu, c1.hi, off, Lw);
-          o1.lo = __shfl_xor_sync(0xffffffffu, c1.lo, off, Lw);
-          o2.hi = __shfl_xor_sync(0xffffffffu, c2.hi, off, Lw);
-          o2.lo = __shfl_xor_sync(0xffffffffu, c2.lo, off, Lw);
-          comp_merge(c1, o1);
-          comp_merge(c2, o2);
-        }
-        if (live && gl == 0) {
-          // cube mean m = C1 / nc and variance (C2 / nc - m^2) / (nc - 1),
-          // in FP32 with the square formed exactly (FMA) and the pairs kept
-          const float inv = (float)A.inv_nc, inv1 = (float)A.inv_nc1;
-          const float mh = c1.hi * inv, ml = c1.lo * inv;
-          const float sq = mh * mh;
-          const float sqe = fmaf(mh, mh, -sq) + 2.0f * mh * ml;
-          const float e2h = c2.hi * inv, e2l = c2.lo * inv;
-          float v = ((e2h - sq) + (e2l - sqe)) * inv1;
-          if (!(v > 0.f)) v = 0.f;
-          comp_merge(tp[0], c1);
-          comp_merge(tp[1], c2);
-          comp_add(tp[2], mh);
-          comp_add(tp[2], ml);
-          comp_add(tp[3], v);
-          if (A.cubes)
-            reinterpret_cast<float4*>(A.cubes)[c] = make_float4(c1.hi, c1.lo, c2.hi, c2.lo);
-        }
+        tp[0] = sw.p;
+        tp[1] = sw2.p;
       } else {
-        double c1 = p1, c2 = p2;
-        for (int off = Lw >> 1; off > 0; off >>= 1) {
-          c1 += __shfl_xor_sync(0xffffffffu, c1, off, Lw);
-          c2 += __shfl_xor_sync(0xffffffffu, c2, off, Lw);
+        t[0] = sw.value();
+        t[1] = sw2.value();
+      }
+    } else {
+      // Groups of Lw lanes share a hypercube; lane j of a group takes the
+      // cube's points j, j + Lw, ... in lock-step with the rest of the CTA
+      // (one tile per step); the group then reduces its sums with a fixed
+      // xor-butterfly (deterministic).  Group i takes cube
+      // (i * cube_mul) mod ncubes, so that the groups of a CTA sit in
+      // unrelated cubes and spread over the bins.
+      const int Lw = A.lanes;
+      const int gl = tid & (Lw - 1);
+      const uint32_t groups_per_cta = blockDim.x / Lw;
+      const uint32_t gstride = gridDim.x * groups_per_cta;
+      const uint32_t gfirst = blockIdx.x * groups_per_cta;
+      const uint32_t rounds = gfirst < A.ncubes ? (A.ncubes - gfirst + gstride - 1) / gstride : 0;
+      const uint32_t cmask = A.ncubes - 1u;
+      const uint32_t per_lane = (A.nc + Lw - 1) / Lw;
+      uint32_t gi = gfirst + tid / Lw;
+      int pend = 0;  // points per thread since the last gather (uniform in the CTA)
+      for (uint32_t r = 0; r < rounds; ++r, gi += gstride) {
+        const bool live = gi < A.ncubes;  // uniform within a group
+        const uint32_t c = A.cube_mul == 1u ? gi : (gi * A.cube_mul) & cmask;
+        if (live) {
+          uint32_t rest = c;
+  #pragma unroll
+          for (int a = 0; a < DM; ++a)
+            if (a < d) {
+              if (A.g_pow2) {
+                cd[a] = (int)(rest & (uint32_t)(A.g - 1));
+                rest >>= A.g_log2;
+              } else {
+                cd[a] = (int)(rest % (uint32_t)A.g);
+                rest /= (uint32_t)A.g;
+              }
+            }
         }
-        if (live && gl == 0) {
-          const double m = c1 * A.inv_nc;
-          double v = (c2 * A.inv_nc - m * m) * A.inv_nc1;
-          if (v < 0.0) v = 0.0;
-          t[0] += c1;
-          t[1] += c2;
-          t[2] += m;
-          t[3] += v;
-          if (A.cubes) {
-            reinterpret_cast<double*>(A.cubes)[2 * (size_t)c] = c1;
-            reinterpret_cast<double*>(A.cubes)[2 * (size_t)c + 1] = c2;
+        const uint32_t s0 = c * A.nc;
+        // a lane's chain of points in one cube is short: plain sums in H,
+        // compensated merges across the group; pmax: the largest weight (for
+        // the per-cube maxima of the integration phase)
+        H p1 = H(0), p2 = H(0), pmax = H(0);
+        if constexpr (PAIR) {
+          for (uint32_t i = 0; i < per_lane; i += 2) {
+            const uint32_t j0 = gl + i * Lw, j1 = j0 + Lw;
+            const bool v0 = live && j0 < A.nc, v1 = live && j1 < A.nc;
+            int kb0[DM], kb1[DM];
+            const H w0 = eval_point(s0 + j0, kb0, v0);
+            const H w1 = eval_point(s0 + j1, kb1, v1);
+            if (v0) {
+              p1 += w0;
+              p2 += w0 * w0;
+              pmax = max(pmax, w0);
+              scatter(kb0, w0);
+            }
+            if (v1) {
+              p1 += w1;
+              p2 += w1 * w1;
+              pmax = max(pmax, w1);
+              scatter(kb1, w1);
+            }
+            if ((pend += 2) >= A.ppt) {
+              gather();
+              pend = 0;
+            }
+          }
+        } else {
+          for (uint32_t i = 0; i < per_lane; ++i) {
+            const uint32_t j = gl + i * Lw;
+            if (live && j < A.nc) {
+              int kb[DM];
+              const H w = eval_point(s0 + j, kb);
+              p1 += w;
+              p2 += w * w;
+              pmax = max(pmax, w);
+              scatter(kb, w);
+            }
+            if (++pend == A.ppt) {
+              gather();
+              pend = 0;
+            }
+          }
+        }
+        if (A.cube_max) {  // integration phase: per-cube maxima (one group per cube)
+          for (int off = Lw >> 1; off > 0; off >>= 1) pmax = max(pmax, __shfl_xor_sync(0xffffffffu, pmax, off, Lw));
+          if (live && gl == 0) A.cube_max[c] = fmax(A.cube_max[c], (double)pmax);
+        }
+        if constexpr (COMP) {
+          fpair c1{p1, 0.f}, c2{p2, 0.f};
+          for (int off = Lw >> 1; off > 0; off >>= 1) {
+            fpair o1, o2;
+            o1.hi = __shfl_xor_sync(0xffffffffu, c1.hi, off, Lw);
+            o1.lo = __shfl_xor_sync(0xffffffffu, c1.lo, off, Lw);
+            o2.hi = __shfl_xor_sync(0xffffffffu, c2.hi, off, Lw);
+            o2.lo = __shfl_xor_sync(0xffffffffu, c2.lo, off, Lw);
+            comp_merge(c1, o1);
+            comp_merge(c2, o2);
+          }
+          if (live && gl == 0) {
+            // cube mean m = C1 / nc and variance (C2 / nc - m^2) / (nc - 1),
+            // in FP32 with the square formed exactly (FMA) and the pairs kept
+            const float inv = (float)A.inv_nc, inv1 = (float)A.inv_nc1;
+            const float mh = c1.hi * inv, ml = c1.lo * inv;
+            const float sq = mh * mh;
+            const float sqe = fmaf(mh, mh, -sq) + 2.0f * mh * ml;
+            const float e2h = c2.hi * inv, e2l = c2.lo * inv;
+            float v = ((e2h - sq) + (e2l - sqe)) * inv1;
+            if (!(v > 0.f)) v = 0.f;
+            comp_merge(tp[0], c1);
+            comp_merge(tp[1], c2);
+            comp_add(tp[2], mh);
+            comp_add(tp[2], ml);
+            comp_add(tp[3], v);
+            if (A.cubes)
+              reinterpret_cast<float4*>(A.cubes)[c] = make_float4(c1.hi, c1.lo, c2.hi, c2.lo);
+          }
+        } else {
+          double c1 = p1, c2 = p2;
+          for (int off = Lw >> 1; off > 0; off >>= 1) {
+            c1 += __shfl_xor_sync(0xffffffffu, c1, off, Lw);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, off, Lw);
+          }
+          if (live && gl == 0) {
+            const double m = c1 * A.inv_nc;
+            double v = (c2 * A.inv_nc - m * m) * A.inv_nc1;
+            if (v < 0.0) v = 0.0;
+            t[0] += c1;
+            t[1] += c2;
+            t[2] += m;
+            t[3] += v;
+            if (A.cubes) {
+              reinterpret_cast<double*>(A.cubes)[2 * (size_t)c] = c1;
+              reinterpret_cast<double*>(A.cubes)[2 * (size_t)c + 1] = c2;
+            }
           }
         }
       }
+      if (pend) gather();
     }
-    if (pend) gather();
-  }
+  };
+  if (bins)
+    pass(BoolTag<true>{});
+  else
+    pass(BoolTag<false>{});
   __syncthreads();
 
   // Partial row of this CTA: histogram cells (FP64, or compensated FP32
   // pairs) including the overflow cells, then the totals.
   const int np = A.nparts, row = blockIdx.x;
-  for (int i = tid; i < 2 * dN; i += blockDim.x) {
+  for (int i = tid; bins && i < 2 * dN; i += blockDim.x) {
     if constexpr (COMP) {
       const fpair p = hist.pair(i);
       reinterpret_cast<float2*>(A.part_bins)[(size_t)i * np + row] = make_float2(p.hi, p.lo);
@@ -677,6 +696,10 @@ __global__ void __launch_bounds__(kSampleMaxThreads<SPEC>) k_sample(const Sample
 template <typename T, int ACC>
 __host__ __device__ inline size_t sample_smem_bytes(int d, int N, int cap) {
   return SmemLayout<T, ACC>::total(d * N, cap);
+}
+template <typename T, int ACC>
+__host__ __device__ inline size_t sample_smem_nobins(int d, int N) {
+  return SmemLayout<T, ACC>::hist(d * N);
 }
 
 // Steps 2-3 for a list of sample indices (parity checks and debugging):
@@ -992,6 +1015,7 @@ inline KernelEntry make_entry() {
   else
     e.spring_spec = nullptr;
   e.smem = &sample_smem_bytes<T, ACC>;
+  e.smem_nobins = &sample_smem_nobins<T, ACC>;
   e.dm = DM;
   e.spec_ppt_min = kPairPoints<T, DM, true> ? 2 : 1;
   return e;

@@ -326,3 +326,28 @@ def test_bases_wmunu_fp64_matches_the_oracle(gv, orc):
     assert abs(r["I"] - ref["I"]) <= 1e-11 * abs(ref["I"])
     assert abs(r["sigma"] - ref["sigma"]) <= 1e-9 * ref["sigma"]
     assert np.max(np.abs(edges - e)) < 1e-11
+
+
+@pytest.mark.parametrize("precision,nstrat,ncall", [(0, 0, 20011), (2, 0, 65613), (0, 4, 4 ** 4 * 40),
+                                                    (2, 4, 4 ** 4 * 40)])
+def test_frozen_grid_passes_skip_only_the_bin_sums(gv, orc, precision, nstrat, ncall):
+    """Passes that do not refine skip the per-bin histogram (only step 5
+    reads it) and run on their own launch shape: their estimates equal those
+    of evaluation passes (which keep it) on the same grid and counters, up to
+    the order of the per-CTA sums; the bin sums stay those of the last pass
+    that formed them."""
+    d = 4
+    p = wl.double_gaussian_params()
+    with gv.vegas_create(wl.DOUBLE_GAUSSIAN, d, p, ncall=ncall, nstrat=nstrat, precision=precision,
+                         ybits=24) as ctx:
+        gv.vegas_iterate(ctx, 2, refine=True)
+        _, bins0 = gv.vegas_get_grid(ctx, bin_sums=True)
+        gv.vegas_reset_results(ctx)
+        gv.vegas_iterate(ctx, 3, refine=False)
+        hist = gv.vegas_get_history(ctx)
+        _, bins1 = gv.vegas_get_grid(ctx, bin_sums=True)
+        ev = np.array([gv.vegas_eval(ctx, it) for it in (2, 3, 4)])
+    np.testing.assert_array_equal(bins1, bins0)
+    tol = 1e-13 if precision == 0 else 1e-6
+    np.testing.assert_allclose(hist[:, 0], ev[:, 0], rtol=tol)
+    np.testing.assert_allclose(hist[:, 1], ev[:, 1], rtol=1e3 * tol)
