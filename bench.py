@@ -40,27 +40,30 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # Philox, word->bin/position, map, integrand, sums (the roofline's unit of
 # work; the peak is the FP32 issue rate of all SMs at the maximum clock).
 ALGO_OPS = {
-    "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, accumulate=8 * 2 + 2 + 12),
-    # the W integrand counted for the points of the coupling helicity cell
-    # (the adapted grid sends nearly all points there): tan, three logs,
-    # two exponentials for x1 and x2, the eta cut, the density exponent
-    "wmunu": dict(philox=2 * 10 * 6, bins=5 * 8, map=5 * 3, integrand=90, accumulate=5 * 2 + 2 + 12),
-    "user_dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8,
-                         accumulate=8 * 2 + 2 + 12),
-    "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, accumulate=4 * 2 + 4),
+    "dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, histogram=8 * 2, sums=2 + 12),
+    "gauss4": dict(philox=2 * 10 * 6, bins=4 * 7, map=4 * 3, integrand=4 * 3 + 2, histogram=4 * 2, sums=4),
     "rambo5": dict(philox=5 * 10 * 6, bins=20 * 6, map=20 * 3, integrand=5 * 60 + 10 * 8 + 5 * 14 + 10,
-                   accumulate=20 * 2 + 14),
+                   histogram=20 * 2, sums=14),
     "rambo4_adjoint": dict(philox=4 * 10 * 6, bins=16 * 6, map=16 * 3,
-                           integrand=4 * 60 + 6 * 8 + 4 * 14 + 10 + 4 * 6 + 20, accumulate=5 * 7),
+                           integrand=4 * 60 + 6 * 8 + 4 * 14 + 10 + 4 * 6 + 20, sums=5 * 7),
     # per SPRING trial: three Philox blocks (8 point words, 2 cube words,
     # 1 acceptance word), a 16-step bisection over the cube table, bins,
     # map, integrand and the keep decision
     "spring_dgauss8": dict(philox=3 * 10 * 6, cube_search=16 * 3, bins=8 * 6, map=8 * 3,
                            integrand=8 * 4 + 8, keep=10),
+    # the W integrand counted for the points of the coupling helicity cell
+    # (the adapted grid sends nearly all points there): tan, three logs,
+    # two exponentials for x1 and x2, the eta cut, the density exponent
+    "wmunu": dict(philox=2 * 10 * 6, bins=5 * 8, map=5 * 3, integrand=90, histogram=5 * 2, sums=2 + 12),
+    "user_dgauss8": dict(philox=2 * 10 * 6, bins=8 * 8, map=8 * 3, integrand=8 * 4 + 8, histogram=8 * 2,
+                         sums=2 + 12),
 }
+# (`histogram`: the per-bin scatter, 2 per axis, which the passes that leave
+# the grid unchanged skip.)
 # DRAM bytes per launch of the sampling kernel from the committed ncu
-# capture (profiles/); None until captured for the current kernel.
-TRAFFIC = {"dgauss8": 68096, "wmunu": 66560}
+# capture (profiles/), per pass kind (refining, frozen grid); a workload
+# whose kernel changed since its capture has no entry.
+TRAFFIC = {"dgauss8": (81152, 612608)}
 
 
 def _workload(name):
@@ -358,8 +361,9 @@ class Runner:
     """One benchmarked workload: how to build it, run one step, time its
     dominant kernel and run one end-to-end step through the C ABI."""
 
-    def __init__(self, name, gv, stream, rank, precision_override):
+    def __init__(self, name, gv, stream, rank, precision_override, autotune=True):
         self.name, self.gv, self.stream, self.rank = name, gv, stream, rank
+        self.autotune = autotune  # False: the library's default launch shape (profiling runs)
         self.tuned = None  # launch shape the autotuner chose for the benchmarked context
         if name == "genz256":
             from paper_1010_2107_gb300 import workloads as wl
@@ -383,8 +387,9 @@ class Runner:
         if self.mode == "batched":
             h = gv.vegas_batch_create(self.insts, nbins=w["nbins"], seed=w["sample_seed"], precision=prec,
                                       ybits=w["ybits"], stream=self.stream)
-            tuned = gv.vegas_batch_autotune(h)
-            self.tuned = self.tuned or tuned
+            if self.autotune:
+                tuned = gv.vegas_batch_autotune(h)
+                self.tuned = self.tuned or tuned
             return h
         kw = dict(nbins=w["nbins"], ncall=w["ncall"], nstrat=w["nstrat"], seed=w["seed"],
                   instance=rank_instance(0, self.rank, self.mode), precision=prec, ybits=w["ybits"],
@@ -396,10 +401,11 @@ class Runner:
         if self.mode == "adjoint":  # the grid the gradient is taken on
             gv.vegas_iterate(h, w["warmup_iters"], refine=True)
         elif self.mode == "spring":  # the BASES run whose integration phase bounds the cubes
-            tuned = gv.vegas_autotune(h)
-            self.tuned = self.tuned or tuned
+            if self.autotune:
+                tuned = gv.vegas_autotune(h)
+                self.tuned = self.tuned or tuned
             gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
-        else:
+        elif self.autotune:
             tuned = gv.vegas_autotune(h)
             self.tuned = self.tuned or tuned
         return h
@@ -488,14 +494,34 @@ class Runner:
         if self.mode == "spring":
             return "k_spring", gv.spring_profile(h, self.w["ntrials"], 5), self.w["ntrials"], {}
         p = gv.vegas_profile_pass(h, 20)
-        return "k_sample", p["sample"], self.w["ncall"], {"finish_ms": p["finish"]}
+        other = {"finish_ms": p["finish"]}
+        if self.mode == "bases":
+            # the step's mix: ITMX1 refining passes with the per-bin histogram,
+            # ITMX2 frozen-grid passes without it
+            q = gv.vegas_profile_frozen_pass(h, 20)
+            n1, n2 = self.w["itmx1"], self.w["itmx2"]
+            ops = ALGO_OPS.get(self.name, {})
+            on, off = sum(ops.values()), sum(v for k, v in ops.items() if k != "histogram")
+            other["launch_kinds"] = [
+                {"kind": "refining pass", "launches_per_step": n1, "ms_per_launch": p["sample"], "ops_per_point": on},
+                {"kind": "frozen-grid pass", "launches_per_step": n2, "ms_per_launch": q["sample"],
+                 "ops_per_point": off}]
+            other["finish_ms_frozen"] = q["finish"]
+            return "k_sample", (n1 * p["sample"] + n2 * q["sample"]) / (n1 + n2), self.w["ncall"], other
+        return "k_sample", p["sample"], self.w["ncall"], other
 
     def ops_per_point(self):
         if self.mode == "batched":
             tot = sum(i["ncall"] for i in self.insts)
             return sum(_genz_ops(i) * i["ncall"] for i in self.insts) / tot
         ops = ALGO_OPS.get(self.name)
-        return sum(ops.values()) if ops else None
+        if not ops:
+            return None
+        if self.mode == "bases":  # launch-weighted over the step's refining and frozen-grid passes
+            n1, n2 = self.w["itmx1"], self.w["itmx2"]
+            on, off = sum(ops.values()), sum(v for k, v in ops.items() if k != "histogram")
+            return (n1 * on + n2 * off) / (n1 + n2)
+        return sum(ops.values())
 
     def launch(self, h):
         gv = self.gv
@@ -551,7 +577,7 @@ def run_ours(args):
     # the library would replace by a stream of its own).
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    R = Runner(args.workload, gv, stream, rank, args.precision)
+    R = Runner(args.workload, gv, stream, rank, args.precision, autotune=not args.no_autotune)
     prec = R.precision()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -591,12 +617,19 @@ def run_ours(args):
         achieved = ops_pt * units / (kms * 1e-3) / 1e12
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = sms * 128 * mhz * 1e6 / 1e12
+        traffic = TRAFFIC.get(args.workload)
+        if traffic is not None and R.mode == "bases":  # launch-weighted like the time
+            traffic = (R.w["itmx1"] * traffic[0] + R.w["itmx2"] * traffic[1]) / (R.w["itmx1"] + R.w["itmx2"])
+        elif traffic is not None:
+            traffic = traffic[0]
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get(args.workload), "kernel": kname, "ops_per_point": round(ops_pt, 1),
+                "traffic": traffic, "kernel": kname, "ops_per_point": round(ops_pt, 1),
                 "points_per_launch": units, "ms_per_launch": kms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)"}
         if prec == gv.FP64:
             roof["note"] = "FP64 form: bound by the FP64 pipe, see fp64_rate"
+        if "launch_kinds" in other:
+            roof["launch_kinds"] = other["launch_kinds"]
     extra = dict(other)
     if R.mode in ("bases", "vegas"):
         launch = gv.vegas_get_launch(h)
@@ -711,6 +744,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape (profiler runs, where the autotuner's timings are skewed)")
     ap.add_argument("--microbench", action="store_true",
                     help="print the measured instruction-class rates (ALU roofline denominators)")
     args = ap.parse_args()

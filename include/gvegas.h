@@ -367,6 +367,11 @@ vegas_status vegas_autotune(vegas_ctx* ctx, int* threads, int* points_per_thread
  * Synchronises the stream. */
 vegas_status vegas_profile_pass(vegas_ctx* ctx, int n_pass, double* ms);
 
+/* The same for the passes that leave the grid unchanged (vegas_iterate with
+ * refine = 0, the integration phase of bases_integrate): no per-bin
+ * histogram, their own launch shape. */
+vegas_status vegas_profile_frozen_pass(vegas_ctx* ctx, int n_pass, double* ms);
+
 /* ------------------------------------------------------------------------
  * Batched integration: n independent VEGAS integrations iterated together,
  * each iteration one persistent kernel over all instances plus one

@@ -1230,7 +1230,25 @@ vegas_status vegas_grad(vegas_ctx* c, uint32_t it, double* grad, double* I) {
   return VEGAS_OK;
 }
 
-vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
+}  // extern "C"
+
+namespace {
+vegas_status profile_passes(vegas_ctx* c, int n_pass, bool nobins, double* ms);
+}  // namespace
+
+extern "C" {
+
+vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) { return profile_passes(c, n_pass, false, ms); }
+
+vegas_status vegas_profile_frozen_pass(vegas_ctx* c, int n_pass, double* ms) {
+  return profile_passes(c, n_pass, true, ms);
+}
+
+}  // extern "C"
+
+namespace {
+
+vegas_status profile_passes(vegas_ctx* c, int n_pass, bool nobins, double* ms) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
   if (n_pass < 1 || !ms) return c->fail(VEGAS_EINVAL, "need n_pass >= 1 and ms[3]");
   CK(c, cudaStreamSynchronize(c->stream));
@@ -1244,11 +1262,13 @@ vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
   double acc[3] = {0, 0, 0};
   cudaError_t e = cudaSuccess;
   for (int p = 0; p < n_pass && e == cudaSuccess; ++p) {
-    gv::SampleArgs A = sample_args(c, (int)(it & 0x7FFFFFFFu));
+    gv::SampleArgs A = sample_args(c, (int)(it & 0x7FFFFFFFu), nobins);
     void* args[] = {&A};
-    gv::FinArgs F = fin_args(c, 0, 0);
+    gv::FinArgs F = fin_args(c, 0, 0, nobins);
     e = cudaEventRecord(ev[0], c->stream);
-    if (!e) e = cudaLaunchKernel(c->ke.sample, dim3(c->ctas), dim3(c->threads), args, c->smem, c->stream);
+    if (!e)
+      e = cudaLaunchKernel(c->ke.sample, dim3(nobins ? c->ctas_nb : c->ctas), dim3(c->threads), args,
+                           nobins ? c->smem_nb : c->smem, c->stream);
     if (!e) e = cudaEventRecord(ev[1], c->stream);
     if (!e) e = gv_launch_finish(&F, c->stream);
     if (!e) e = cudaEventRecord(ev[2], c->stream);
@@ -1266,6 +1286,10 @@ vegas_status vegas_profile_pass(vegas_ctx* c, int n_pass, double* ms) {
   for (int k = 0; k < 3; ++k) ms[k] = acc[k] / n_pass;
   return VEGAS_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int vegas_ntheta(const vegas_ctx* c) {
   if (!c) return 0;

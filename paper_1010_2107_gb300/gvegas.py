@@ -99,6 +99,7 @@ _SIGS = {
     "vegas_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
     "vegas_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_profile_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
+    "vegas_profile_frozen_pass": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_microbench": (ctypes.c_int, [ctypes.c_int, _DP]),
     "vegas_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
@@ -393,6 +394,14 @@ def vegas_profile_pass(ctx: Context, n_pass: int = 10):
     (reduction of the partials) and the two together."""
     ms = np.zeros(3)
     _check(lib().vegas_profile_pass(ctx.handle, int(n_pass), _dp(ms)), ctx.handle)
+    return dict(sample=ms[0], finish=ms[1], passes=ms[2])
+
+
+def vegas_profile_frozen_pass(ctx: Context, n_pass: int = 10):
+    """As vegas_profile_pass for the passes that leave the grid unchanged (no
+    per-bin histogram, their own launch shape)."""
+    ms = np.zeros(3)
+    _check(lib().vegas_profile_frozen_pass(ctx.handle, int(n_pass), _dp(ms)), ctx.handle)
     return dict(sample=ms[0], finish=ms[1], passes=ms[2])
 
 
