@@ -436,8 +436,8 @@ class Runner:
             return 2 + 2 + 2 * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return 2
-        if self.mode == "spring":  # cube table, trials, compaction
-            return 3
+        if self.mode == "spring":  # cube table (4 kernels), trials, compaction
+            return 6
         return 2 + 2 + 2 * w["itmx"]
 
     def step(self, h):

@@ -82,6 +82,10 @@ struct vegas_ctx {
   // SPRING buffers (grown on demand)
   uint64_t* d_q = nullptr;
   uint64_t* d_prefix = nullptr;
+  double* d_mt = nullptr;          // [G] cube bounds q_c / scale
+  uint64_t* d_psample = nullptr;   // sampled prefix sums (first level of the cube search)
+  double* d_bmax = nullptr;        // per-block maxima and sums of the table kernels
+  unsigned long long* d_bsum = nullptr;
   double* d_meta = nullptr;        // {Q, scale, status}
   double* d_stage_x = nullptr;     // [n][d]
   uint64_t* d_stage_t = nullptr;   // [n]
@@ -168,22 +172,81 @@ void destroy_graphs(vegas_ctx* c) {
 
 // Launch geometry: a persistent grid of CTAs per SM as occupancy allows
 // (or as requested), capped by the work available.
-// SPRING table (one block): M = largest recorded maximum (after the output
-// scale); scale = 2^24 / M; q_c = ceil(M_c scale) in FP64 as the oracle
-// computes it; exclusive prefix sums P[0..G] in 64-bit integers.  meta:
-// {Q, scale, status} (status 1: no positive maximum).
-__global__ void k_spring_table(const double* cmax, uint32_t G, double out_scale, uint64_t* q, uint64_t* prefix,
-                               double* meta) {
-  __shared__ double smax[32];
-  __shared__ unsigned long long ssum[1024];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  double m = 0.0;
-  for (uint32_t i = tid; i < G; i += nt) m = fmax(m, cmax[i] * out_scale);
+// SPRING table, in four small kernels over blocks of kSpan cubes (every
+// FP64 operation of a cube is the oracle's, in the oracle's order; the
+// integer sums are exact in any order):
+//   k_spring_max      per-block maxima of M_c = cmax_c * out_scale;
+//   k_spring_weights  M = the largest M_c, scale = 2^24 / M,
+//                     q_c = ceil(M_c scale), the bound mt_c = q_c / scale,
+//                     per-block sums of q;
+//   k_spring_scan     (one block) exclusive scan of the block sums,
+//                     P[G] = Q, meta = {Q, scale, status} (status 1: no
+//                     positive maximum);
+//   k_spring_prefix   exclusive prefix sums P[0..G) in 64-bit integers and
+//                     their sample psample[j] = P[j 2^psh].
+constexpr int kSpanThreads = 256, kSpanPer = 4;
+constexpr uint32_t kSpan = kSpanThreads * kSpanPer;  // cubes per block
+
+__device__ double block_max_d(double m, double* sm) {
   for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if ((tid & 31) == 0) smax[tid >> 5] = m;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
   __syncthreads();
   double M = 0.0;
-  for (int w = 0; w < nt / 32; ++w) M = fmax(M, smax[w]);
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, sm[w]);
+  return M;
+}
+
+__global__ void __launch_bounds__(kSpanThreads) k_spring_max(const double* cmax, uint32_t G, double out_scale,
+                                                             double* bmax) {
+  __shared__ double sm[32];
+  const uint32_t lo = blockIdx.x * kSpan, hi = min(lo + kSpan, G);
+  double m = 0.0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) m = fmax(m, cmax[i] * out_scale);
+  m = block_max_d(m, sm);
+  if (threadIdx.x == 0) bmax[blockIdx.x] = m;
+}
+
+// The largest of the block maxima (any order: max is exact).
+__device__ double spring_global_max(const double* bmax, uint32_t nb, double* sm) {
+  double m = 0.0;
+  for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, bmax[i]);
+  return block_max_d(m, sm);
+}
+
+__global__ void __launch_bounds__(kSpanThreads) k_spring_weights(const double* cmax, uint32_t G, double out_scale,
+                                                                 const double* bmax, uint32_t nb, uint64_t* q,
+                                                                 double* mt, unsigned long long* bsum) {
+  __shared__ double sm[32];
+  __shared__ unsigned long long ss[32];
+  const double M = spring_global_max(bmax, nb, sm);
+  if (!(M > 0.0) || !isfinite(M)) return;  // k_spring_scan reports it
+  const double scale = 16777216.0 / M;
+  const uint32_t lo = blockIdx.x * kSpan, hi = min(lo + kSpan, G);
+  unsigned long long sum = 0;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double v = cmax[i] * out_scale;
+    const uint64_t qi = v > 0.0 ? (uint64_t)ceil(v * scale) : 0ull;
+    q[i] = qi;
+    mt[i] = (double)qi / scale;  // the cube's bound in the integrand's units
+    sum += qi;
+  }
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if ((threadIdx.x & 31) == 0) ss[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ss[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_spring_scan(const double* bmax, uint32_t nb, unsigned long long* bsum,
+                                                      uint32_t G, uint64_t* prefix, double* meta) {
+  __shared__ double sm[32];
+  __shared__ unsigned long long ssum[1024];
+  const double M = spring_global_max(bmax, nb, sm);
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (!(M > 0.0) || !isfinite(M)) {
     if (tid == 0) {
       meta[0] = 0.0;
@@ -192,18 +255,13 @@ __global__ void k_spring_table(const double* cmax, uint32_t G, double out_scale,
     }
     return;
   }
-  const double scale = 16777216.0 / M;
-  const uint32_t per = (G + nt - 1) / nt, lo = min((uint32_t)tid * per, G), hi = min(lo + per, G);
+  // exclusive scan of bsum[0..nb) in place: contiguous runs per thread
+  const uint32_t per = (nb + nt - 1) / nt, lo = min((uint32_t)tid * per, nb), hi = min(lo + per, nb);
   unsigned long long sum = 0;
-  for (uint32_t i = lo; i < hi; ++i) {
-    const double v = cmax[i] * out_scale;
-    const uint64_t qi = v > 0.0 ? (uint64_t)ceil(v * scale) : 0ull;
-    q[i] = qi;
-    sum += qi;
-  }
+  for (uint32_t i = lo; i < hi; ++i) sum += bsum[i];
   ssum[tid] = sum;
   __syncthreads();
-  if (tid == 0) {  // exclusive scan of the thread sums (integers: any order is exact)
+  if (tid == 0) {
     unsigned long long run = 0;
     for (int k = 0; k < nt; ++k) {
       const unsigned long long v = ssum[k];
@@ -212,14 +270,51 @@ __global__ void k_spring_table(const double* cmax, uint32_t G, double out_scale,
     }
     prefix[G] = run;
     meta[0] = (double)run;
-    meta[1] = scale;
+    meta[1] = 16777216.0 / M;
     meta[2] = 0.0;
   }
   __syncthreads();
   unsigned long long run = ssum[tid];
   for (uint32_t i = lo; i < hi; ++i) {
-    prefix[i] = run;
-    run += q[i];
+    const unsigned long long v = bsum[i];
+    bsum[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSpanThreads) k_spring_prefix(const uint64_t* q, uint32_t G,
+                                                                const unsigned long long* boff, uint64_t* prefix,
+                                                                uint64_t* psample, uint32_t psh, const double* meta) {
+  __shared__ unsigned long long sw[32];
+  if (meta[2] != 0.0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lo = blockIdx.x * kSpan + (uint32_t)tid * kSpanPer;
+  uint64_t v[kSpanPer];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kSpanPer; ++k) {
+    v[k] = lo + k < G ? q[lo + k] : 0ull;
+    s += v[k];
+  }
+  // exclusive scan of the thread sums: within the warp, then over the warps
+  unsigned long long inc = s;
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += o;
+  }
+  if (lane == 31) sw[warp] = inc;
+  __syncthreads();
+  unsigned long long run = boff[blockIdx.x] + inc - s;
+  for (int w = 0; w < warp; ++w) run += sw[w];
+  const uint32_t smask = (1u << psh) - 1u;
+#pragma unroll
+  for (int k = 0; k < kSpanPer; ++k) {
+    const uint32_t i = lo + k;
+    if (i < G) {
+      prefix[i] = run;
+      if ((i & smask) == 0) psample[i >> psh] = run;
+    }
+    run += v[k];
   }
 }
 
@@ -649,7 +744,7 @@ void vegas_destroy(vegas_ctx* c) {
   cudaFree(c->d_tot);
   cudaFree(c->d_cubes);
   cudaFree(c->d_cube_max);
-  for (void* p : {(void*)c->d_q, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
+  for (void* p : {(void*)c->d_q, (void*)c->d_mt, (void*)c->d_psample, (void*)c->d_bmax, (void*)c->d_bsum, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
                   (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
     cudaFree(p);
   cudaFree(c->d_gpart);
@@ -888,8 +983,16 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
     return VEGAS_OK;
   };
   vegas_status st = VEGAS_OK;
+  uint32_t psh = 0;  // sample stride 2^psh: at most 4096 sampled prefixes (32 KB) per CTA
+  while ((c->ncubes + (1ull << psh) - 1) >> psh > 4096) ++psh;
+  const uint32_t nsample = (uint32_t)((c->ncubes + (1ull << psh) - 1) >> psh);
   if (!c->d_q) {
     if (!st) st = grow((void**)&c->d_q, sizeof(uint64_t) * c->ncubes);
+    if (!st) st = grow((void**)&c->d_mt, sizeof(double) * c->ncubes);
+    if (!st) st = grow((void**)&c->d_psample, sizeof(uint64_t) * nsample);
+    const size_t nb = (c->ncubes + kSpan - 1) / kSpan;
+    if (!st) st = grow((void**)&c->d_bmax, sizeof(double) * nb);
+    if (!st) st = grow((void**)&c->d_bsum, sizeof(unsigned long long) * nb);
     if (!st) st = grow((void**)&c->d_prefix, sizeof(uint64_t) * (c->ncubes + 1));
     if (!st) st = grow((void**)&c->d_meta, sizeof(double) * 3);
     if (!st) st = grow((void**)&c->d_counters, sizeof(unsigned long long) * 2);
@@ -910,14 +1013,24 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
     return st;
   }
   // integer cube table from the recorded maxima (in the integrand's units)
-  k_spring_table<<<1, 1024, 0, c->stream>>>(c->d_cube_max, (uint32_t)c->ncubes, c->scale, c->d_q, c->d_prefix,
-                                            c->d_meta);
+  {
+    const uint32_t G = (uint32_t)c->ncubes, nb = (G + kSpan - 1) / kSpan;
+    k_spring_max<<<nb, kSpanThreads, 0, c->stream>>>(c->d_cube_max, G, c->scale, c->d_bmax);
+    k_spring_weights<<<nb, kSpanThreads, 0, c->stream>>>(c->d_cube_max, G, c->scale, c->d_bmax, nb, c->d_q,
+                                                         c->d_mt, c->d_bsum);
+    k_spring_scan<<<1, 1024, 0, c->stream>>>(c->d_bmax, nb, c->d_bsum, G, c->d_prefix, c->d_meta);
+    k_spring_prefix<<<nb, kSpanThreads, 0, c->stream>>>(c->d_q, G, c->d_bsum, c->d_prefix, c->d_psample, psh,
+                                                        c->d_meta);
+  }
   CK(c, cudaGetLastError());
   CK(c, cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 2, c->stream));
   gv::SpringArgs R{};
   R.S = sample_args(c, 0);
   R.prefix = c->d_prefix;
-  R.q = c->d_q;
+  R.mt = c->d_mt;
+  R.psample = c->d_psample;
+  R.nsample = nsample;
+  R.psh = psh;
   R.meta = c->d_meta;
   R.out_scale = c->scale;
   R.trial0 = (uint32_t)trial0;
@@ -929,8 +1042,9 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   R.counts = c->d_counts;
   R.counters = c->d_counters;
   const bool f64 = c->prec == VG_FP64;
-  const size_t smem = (size_t)d * N * (f64 ? sizeof(double2) : sizeof(float2)) +
-                      gv::kNumDerived * (f64 ? sizeof(double) : sizeof(float));
+  const size_t smem = gv::spring_sample_offset(d * N, f64 ? sizeof(double2) : sizeof(float2),
+                                               f64 ? sizeof(double) : sizeof(float)) +
+                      sizeof(uint64_t) * nsample;
   int occ = 0;
   CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem));

@@ -723,17 +723,23 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + (size_t)dN * sizeof(T2));
+  uint64_t* ps = reinterpret_cast<uint64_t*>(smem + spring_sample_offset(dN, sizeof(T2), sizeof(T)));
   __shared__ uint32_t wcount[8];
   __shared__ uint32_t chunk_count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
+  for (uint32_t i = tid; i < R.nsample; i += blockDim.x) ps[i] = R.psample[i];
   __syncthreads();
-  const double Q = R.meta[0], scale = R.meta[1];
+  const double Q = R.meta[0];
   const uint64_t Qi = (uint64_t)Q;
   const uint32_t G = A.ncubes;
   const int W = YB == 24 ? d : 2 * d;
+  // words W .. W+2 (24-bit) or W+3 (53-bit) from the blocks of W >> 2 on:
+  // the second block only when they run past the first
+  const int o = W & 3;
+  const bool two_blocks = o + (YB == 24 ? 3 : 4) > 4;
   unsigned long long ov = 0, np = 0;
   for (uint32_t chunk = blockIdx.x; chunk < R.nchunks; chunk += gridDim.x) {
     if (tid == 0) chunk_count = 0;
@@ -748,13 +754,25 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
         uint32_t wx[8];
         const int g0 = W >> 2;
         const uint4 b0 = philox4x32_10(make_uint4(t, (uint32_t)g0, kSpringIt, A.instance), A.ks);
-        const uint4 b1 = philox4x32_10(make_uint4(t, (uint32_t)(g0 + 1), kSpringIt, A.instance), A.ks);
+        const uint4 b1 = two_blocks ? philox4x32_10(make_uint4(t, (uint32_t)(g0 + 1), kSpringIt, A.instance), A.ks)
+                                    : make_uint4(0u, 0u, 0u, 0u);
         wx[0] = b0.x; wx[1] = b0.y; wx[2] = b0.z; wx[3] = b0.w;
         wx[4] = b1.x; wx[5] = b1.y; wx[6] = b1.z; wx[7] = b1.w;
-        const int o = W & 3;
         const uint64_t U = ((uint64_t)wx[o] << 32) | (uint64_t)wx[o + 1];
         const uint64_t u = __umul64hi(U, Qi);
-        uint32_t lo = 0, hi = G;  // prefix[lo] <= u < prefix[hi]
+        // the cube c with prefix[c] <= u < prefix[c + 1] (the last of equal
+        // prefixes): bisection over the shared-memory sample prefix[j << psh],
+        // then over the 2^psh cubes of the chosen stretch in global memory
+        uint32_t lo = 0, hi = R.nsample;
+        while (hi - lo > 1) {
+          const uint32_t mid = lo + ((hi - lo) >> 1);
+          if (ps[mid] <= u)
+            lo = mid;
+          else
+            hi = mid;
+        }
+        lo <<= R.psh;
+        hi = min(lo + (1u << R.psh), G);
         while (hi - lo > 1) {
           const uint32_t mid = lo + ((hi - lo) >> 1);
           if (__ldg(R.prefix + mid) <= u)
@@ -780,11 +798,12 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
         }
         int kb[DM];  // bins: not needed here
         const T J = make_point<T, DM, YB, SPEC>(A, kSpringIt, t, cd, tab, x, kb, nullptr);
-        const double w = (double)(F<T, DM>::eval(x, d, P) * J) * R.out_scale;
+        double w = (double)(F<T, DM>::eval(x, d, P) * J);
+        if (R.out_scale != 1.0) w *= R.out_scale;
         const double v = YB == 24 ? (double)(wx[o + 2] >> 8) * (1.0 / 16777216.0)
                                   : ((double)(wx[o + 2] >> 5) * 67108864.0 + (double)(wx[o + 3] >> 6)) *
                                         (1.0 / 9007199254740992.0);
-        const double Mt = (double)__ldg(R.q + c) / scale;
+        const double Mt = __ldg(R.mt + c);
         if (!(w > 0.0)) {
           ++np;
         } else if (w > Mt) {
