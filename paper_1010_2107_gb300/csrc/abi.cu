@@ -83,6 +83,7 @@ struct vegas_ctx {
   uint64_t* d_q = nullptr;
   uint64_t* d_prefix = nullptr;
   double* d_mt = nullptr;          // [G] cube bounds q_c / scale
+  float* d_mt32 = nullptr;         // [G] the same in FP32
   uint64_t* d_psample = nullptr;   // sampled prefix sums (first level of the cube search)
   double* d_bmax = nullptr;        // per-block maxima and sums of the table kernels
   unsigned long long* d_bsum = nullptr;
@@ -216,7 +217,7 @@ __device__ double spring_global_max(const double* bmax, uint32_t nb, double* sm)
 
 __global__ void __launch_bounds__(kSpanThreads) k_spring_weights(const double* cmax, uint32_t G, double out_scale,
                                                                  const double* bmax, uint32_t nb, uint64_t* q,
-                                                                 double* mt, unsigned long long* bsum) {
+                                                                 double* mt, float* mt32, unsigned long long* bsum) {
   __shared__ double sm[32];
   __shared__ unsigned long long ss[32];
   const double M = spring_global_max(bmax, nb, sm);
@@ -228,7 +229,9 @@ __global__ void __launch_bounds__(kSpanThreads) k_spring_weights(const double* c
     const double v = cmax[i] * out_scale;
     const uint64_t qi = v > 0.0 ? (uint64_t)ceil(v * scale) : 0ull;
     q[i] = qi;
-    mt[i] = (double)qi / scale;  // the cube's bound in the integrand's units
+    const double b = (double)qi / scale;  // the cube's bound in the integrand's units
+    mt[i] = b;
+    mt32[i] = (float)b;
     sum += qi;
   }
   for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
@@ -744,7 +747,7 @@ void vegas_destroy(vegas_ctx* c) {
   cudaFree(c->d_tot);
   cudaFree(c->d_cubes);
   cudaFree(c->d_cube_max);
-  for (void* p : {(void*)c->d_q, (void*)c->d_mt, (void*)c->d_psample, (void*)c->d_bmax, (void*)c->d_bsum, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
+  for (void* p : {(void*)c->d_q, (void*)c->d_mt, (void*)c->d_mt32, (void*)c->d_psample, (void*)c->d_bmax, (void*)c->d_bsum, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
                   (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
     cudaFree(p);
   cudaFree(c->d_gpart);
@@ -989,6 +992,7 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   if (!c->d_q) {
     if (!st) st = grow((void**)&c->d_q, sizeof(uint64_t) * c->ncubes);
     if (!st) st = grow((void**)&c->d_mt, sizeof(double) * c->ncubes);
+    if (!st) st = grow((void**)&c->d_mt32, sizeof(float) * c->ncubes);
     if (!st) st = grow((void**)&c->d_psample, sizeof(uint64_t) * nsample);
     const size_t nb = (c->ncubes + kSpan - 1) / kSpan;
     if (!st) st = grow((void**)&c->d_bmax, sizeof(double) * nb);
@@ -1017,7 +1021,7 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
     const uint32_t G = (uint32_t)c->ncubes, nb = (G + kSpan - 1) / kSpan;
     k_spring_max<<<nb, kSpanThreads, 0, c->stream>>>(c->d_cube_max, G, c->scale, c->d_bmax);
     k_spring_weights<<<nb, kSpanThreads, 0, c->stream>>>(c->d_cube_max, G, c->scale, c->d_bmax, nb, c->d_q,
-                                                         c->d_mt, c->d_bsum);
+                                                         c->d_mt, c->d_mt32, c->d_bsum);
     k_spring_scan<<<1, 1024, 0, c->stream>>>(c->d_bmax, nb, c->d_bsum, G, c->d_prefix, c->d_meta);
     k_spring_prefix<<<nb, kSpanThreads, 0, c->stream>>>(c->d_q, G, c->d_bsum, c->d_prefix, c->d_psample, psh,
                                                         c->d_meta);
@@ -1028,6 +1032,7 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   R.S = sample_args(c, 0);
   R.prefix = c->d_prefix;
   R.mt = c->d_mt;
+  R.mt32 = c->d_mt32;
   R.psample = c->d_psample;
   R.nsample = nsample;
   R.psh = psh;

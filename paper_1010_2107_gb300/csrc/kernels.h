@@ -153,6 +153,7 @@ struct SpringArgs {
   SampleArgs S;
   const uint64_t* prefix;   // [G + 1] exclusive prefix sums of the integer cube weights
   const double* mt;         // [G] cube bounds q_c / scale (FP64, formed by the table kernel)
+  const float* mt32;        // [G] the same rounded to FP32 (the FP32 kernels' keep decision)
   const uint64_t* psample;  // [nsample] prefix[j << psh]: the first level of the cube search
   uint32_t nsample, psh;    // nsample = ceil(G / 2^psh) (staged in shared memory)
   const double* meta;       // {Q, scale} written by the table kernel

@@ -710,7 +710,8 @@ __host__ __device__ inline size_t sample_smem_nobins(int d, int N) {
 // 0..W-1 place the point as the sampling step does, words W and W+1 pick
 // the cube through the integer prefix sums, the next word (two for 53-bit
 // words) gives v, and the trial is kept iff w > 0 and (w exceeds the cube's
-// bound, or v times the bound is below w), the comparison in FP64.  Each
+// bound, or v times the bound is below w), the comparison in FP64 (in FP32
+// for the FP32 form with 24-bit words, whose weight is FP32).  Each
 // chunk of trials is compacted in trial order (warp ballots, then warps in
 // order).  One thread per trial and round; 256 threads.
 constexpr uint32_t kSpringIt = 0xFFFFFFFFu;
@@ -798,19 +799,37 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
         }
         int kb[DM];  // bins: not needed here
         const T J = make_point<T, DM, YB, SPEC>(A, kSpringIt, t, cd, tab, x, kb, nullptr);
-        double w = (double)(F<T, DM>::eval(x, d, P) * J);
-        if (R.out_scale != 1.0) w *= R.out_scale;
-        const double v = YB == 24 ? (double)(wx[o + 2] >> 8) * (1.0 / 16777216.0)
-                                  : ((double)(wx[o + 2] >> 5) * 67108864.0 + (double)(wx[o + 3] >> 6)) *
-                                        (1.0 / 9007199254740992.0);
-        const double Mt = __ldg(R.mt + c);
-        if (!(w > 0.0)) {
-          ++np;
-        } else if (w > Mt) {
-          ++ov;
-          keep = true;
+        if constexpr (std::is_same<T, float>::value && YB == 24) {
+          // FP32 form: the weight is FP32 already, so the decision is taken
+          // in FP32 too (v is exact in 24 bits; the bound is rounded once);
+          // it departs from the FP64 one only within FP32 rounding of w
+          float w = F<T, DM>::eval(x, d, P) * J;
+          if (R.out_scale != 1.0) w *= (float)R.out_scale;
+          const float v = (float)(wx[o + 2] >> 8) * (1.0f / 16777216.0f);
+          const float Mt = __ldg(R.mt32 + c);
+          if (!(w > 0.f)) {
+            ++np;
+          } else if (w > Mt) {
+            ++ov;
+            keep = true;
+          } else {
+            keep = v * Mt < w;
+          }
         } else {
-          keep = v * Mt < w;
+          double w = (double)(F<T, DM>::eval(x, d, P) * J);
+          if (R.out_scale != 1.0) w *= R.out_scale;
+          const double v = YB == 24 ? (double)(wx[o + 2] >> 8) * (1.0 / 16777216.0)
+                                    : ((double)(wx[o + 2] >> 5) * 67108864.0 + (double)(wx[o + 3] >> 6)) *
+                                          (1.0 / 9007199254740992.0);
+          const double Mt = __ldg(R.mt + c);
+          if (!(w > 0.0)) {
+            ++np;
+          } else if (w > Mt) {
+            ++ov;
+            keep = true;
+          } else {
+            keep = v * Mt < w;
+          }
         }
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, keep);

@@ -5,7 +5,7 @@ oracle so that both sides draw from the same bounds:
 
 * FP64 form: the same kept trials, bit for bit in their indices, the points
   to rounding, the same overflow and non-positive counts;
-* FP32 form (FP32 weights, the keep decision in FP64 on each side's weight):
+* FP32 form (FP32 weights and keep decision on the GPU, FP64 in the oracle):
   at most 0.5 % of trials decided differently, points to FP32 rounding.
 """
 import numpy as np
