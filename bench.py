@@ -63,7 +63,7 @@ ALGO_OPS = {
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/), per pass kind (refining, frozen grid); a workload
 # whose kernel changed since its capture has no entry.
-TRAFFIC = {"dgauss8": (81152, 612608)}
+TRAFFIC = {"dgauss8": (81152, 612608), "wmunu": (79104, 350976)}
 
 
 def _workload(name):
@@ -361,9 +361,10 @@ class Runner:
     """One benchmarked workload: how to build it, run one step, time its
     dominant kernel and run one end-to-end step through the C ABI."""
 
-    def __init__(self, name, gv, stream, rank, precision_override, autotune=True):
+    def __init__(self, name, gv, stream, rank, precision_override, autotune=True, launch=None):
         self.name, self.gv, self.stream, self.rank = name, gv, stream, rank
         self.autotune = autotune  # False: the library's default launch shape (profiling runs)
+        self.fixed_launch = launch  # (threads, points per thread) to set instead of tuning
         self.tuned = None  # launch shape the autotuner chose for the benchmarked context
         if name == "genz256":
             from paper_1010_2107_gb300 import workloads as wl
@@ -405,6 +406,9 @@ class Runner:
                 tuned = gv.vegas_autotune(h)
                 self.tuned = self.tuned or tuned
             gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
+        elif self.fixed_launch:
+            gv.vegas_set_launch(h, self.fixed_launch[0], 0)
+            gv.vegas_set_tile(h, self.fixed_launch[1])
         elif self.autotune:
             tuned = gv.vegas_autotune(h)
             self.tuned = self.tuned or tuned
@@ -577,7 +581,8 @@ def run_ours(args):
     # the library would replace by a stream of its own).
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    R = Runner(args.workload, gv, stream, rank, args.precision, autotune=not args.no_autotune)
+    launch = tuple(int(v) for v in args.launch.split(",")) if args.launch else None
+    R = Runner(args.workload, gv, stream, rank, args.precision, autotune=not args.no_autotune, launch=launch)
     prec = R.precision()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -746,6 +751,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler runs, where the autotuner's timings are skewed)")
+    ap.add_argument("--launch", default=None, metavar="THREADS,PPT",
+                    help="set this launch shape instead of tuning (profiler runs of a tuned shape)")
     ap.add_argument("--microbench", action="store_true",
                     help="print the measured instruction-class rates (ALU roofline denominators)")
     args = ap.parse_args()
