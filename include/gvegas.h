@@ -347,8 +347,10 @@ vegas_status vegas_get_tile(vegas_ctx* ctx, int* points_per_thread, int* cap);
 /* Launch-shape autotuner (the paper tunes nBlockSize by hand, Appendix A):
  * times evaluation passes (as vegas_profile_pass: no refinement, window
  * untouched) for threads per CTA in {128, 256, 384, 512} and histogram
- * tiles in {automatic, 1, 2, 4} points per thread, skipping shapes the
- * kernel cannot take; the three fastest are timed again in three
+ * tiles in {automatic, 1, 2, 4} points per thread, each with the largest
+ * and with the smallest bucket capacity that reaches the tile's best
+ * occupancy, skipping shapes the kernel cannot take; the three fastest are
+ * timed again in three
  * interleaved rounds of five passes, and the one with the best round is
  * kept.  Returns its threads, points
  * per thread and the pass time in ms (any output may be NULL).  The

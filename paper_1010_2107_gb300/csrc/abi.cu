@@ -65,6 +65,7 @@ struct vegas_ctx {
   int ctas_nb = 0;      // CTAs of a pass without the per-bin histogram
   size_t smem_nb = 0;   // and its dynamic shared memory
   int ppt = 1, ppt_req = 0, ppt_min = 1;  // points per thread per histogram tile
+  bool small_cap = false;                 // tile capacity policy (gv::choose_tile)
   size_t smem = 0;
   // device buffers
   double* d_edges = nullptr;
@@ -356,7 +357,7 @@ vegas_status configure_launch(vegas_ctx* c) {
   int occ_cap = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c->ke.sample, c->threads, 0);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
-  const gv::TileShape t = gv::choose_tile(c->threads, N, c->ppt_req, c->ppt_min, occ_cap, occ_of);
+  const gv::TileShape t = gv::choose_tile(c->threads, N, c->ppt_req, c->ppt_min, occ_cap, occ_of, c->small_cap);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   if (t.occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %d points per thread",
                                 c->threads, t.ppt);
@@ -1261,11 +1262,14 @@ vegas_status vegas_autotune(vegas_ctx* c, int* threads, int* points_per_thread, 
   static const int kTiles[] = {0, 1, 2, 4};
   struct Cand {
     int t, p;
+    bool small;
     double ms;
   };
   std::vector<Cand> cands;
-  // one pass of warm-up, then the mean of n passes, for shape (t, p)
-  auto time_shape = [&](int t, int p, int n, double* out) -> vegas_status {
+  // one pass of warm-up, then the mean of n passes, for shape (t, p) and
+  // capacity policy `small`
+  auto time_shape = [&](int t, int p, bool small, int n, double* out) -> vegas_status {
+    c->small_cap = small;
     if (vegas_set_launch(c, t, 0) != VEGAS_OK || vegas_set_tile(c, p) != VEGAS_OK) return VEGAS_EINVAL;
     double m[3];
     vegas_status st = vegas_profile_pass(c, 1, m);
@@ -1276,10 +1280,15 @@ vegas_status vegas_autotune(vegas_ctx* c, int* threads, int* points_per_thread, 
   // screening: every shape the kernel takes (the others are skipped)
   for (int t : kThreads)
     for (int p : kTiles) {
-      double m = 0.0;
-      const vegas_status st = time_shape(t, p, 3, &m);
-      if (st == VEGAS_ECUDA) return c->err.empty() ? c->fail(st, "autotune: pass failed") : st;
-      if (st == VEGAS_OK) cands.push_back({t, p, m});
+      int cap_large = -1;  // the tile of the largest-capacity policy (a repeat is not timed twice)
+      for (bool small : {false, true}) {
+        double m = 0.0;
+        const vegas_status st = time_shape(t, p, small, 3, &m);
+        if (st == VEGAS_ECUDA) return c->err.empty() ? c->fail(st, "autotune: pass failed") : st;
+        if (st != VEGAS_OK || (small && c->cap == cap_large)) continue;
+        if (!small) cap_large = c->cap;
+        cands.push_back({t, p, small, m});
+      }
     }
   if (cands.empty()) return c->fail(VEGAS_EINVAL, "autotune: no launch shape fits");
   // the three fastest again, in interleaved rounds, keeping each one's best
@@ -1289,11 +1298,12 @@ vegas_status vegas_autotune(vegas_ctx* c, int* threads, int* points_per_thread, 
   for (int r = 0; r < 3; ++r)
     for (Cand& k : cands) {
       double m = 0.0;
-      if (time_shape(k.t, k.p, 5, &m) != VEGAS_OK) return c->fail(VEGAS_ECUDA, "autotune: pass failed");
+      if (time_shape(k.t, k.p, k.small, 5, &m) != VEGAS_OK) return c->fail(VEGAS_ECUDA, "autotune: pass failed");
       k.ms = r == 0 ? m : std::min(k.ms, m);
     }
   const Cand best = *std::min_element(cands.begin(), cands.end(),
                                       [](const Cand& a, const Cand& b) { return a.ms < b.ms; });
+  c->small_cap = best.small;
   vegas_status st = vegas_set_launch(c, best.t, 0);
   if (!st) st = vegas_set_tile(c, best.p);
   if (st) return st;

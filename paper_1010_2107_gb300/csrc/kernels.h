@@ -90,9 +90,13 @@ struct TileShape {
 // most the kernel can have) wins; ppt_req > 0 forces the tile and then halves
 // the capacity until it fits.  A kernel that evaluates ppt_min points per
 // thread at a time (1 or 2) gets tiles that are multiples of it.
-// occ_of(cap, ppt) returns the CTAs per SM (0: does not fit).
+// occ_of(cap, ppt) returns the CTAs per SM (0: does not fit).  With
+// `small_cap` the smallest capacity of the range that reaches the best
+// occupancy is taken (less to gather, more claims spilling past the
+// buckets), else the largest.
 template <class OccOf>
-inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int occ_cap, OccOf occ_of) {
+inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int occ_cap, OccOf occ_of,
+                             bool small_cap = false) {
   auto ceil4 = [](double v) { return ((int)v + 1 + 3) & ~3; };
   TileShape best{0, 0, 0};
   const int wanted = occ_cap * threads / 32 < 16 ? occ_cap * threads / 32 : 16;
@@ -108,8 +112,8 @@ inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int o
     TileShape t{ppt, hi, 0};
     for (int cap = hi; cap >= lo; cap -= 4) {
       const int o = occ_of(cap, ppt);
-      if (o > t.occ) t = TileShape{ppt, cap, o};
-      if (o >= occ_cap) break;
+      if (o > t.occ || (small_cap && o == t.occ && o > 0)) t = TileShape{ppt, cap, o};
+      if (o >= occ_cap && !small_cap) break;
     }
     if (ppt_req > 0) {  // forced tile: shrink the capacity until it fits
       for (int cap = lo; t.occ < 1 && cap > 4;) {
