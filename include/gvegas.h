@@ -411,8 +411,9 @@ vegas_status vegas_batch_get_history(vegas_batch* batch, int i, double* hist, in
 vegas_status vegas_batch_set_launch(vegas_batch* batch, int threads, int rounds);
 vegas_status vegas_batch_get_launch(vegas_batch* batch, int* threads, int* rounds, int* ctas, int* items);
 
-/* Autotuner: times every (threads, rounds) candidate on the batch's own
- * workload (an evaluation pass, nothing recorded), times the three fastest
+/* Autotuner: times every (threads, rounds) candidate, each with the largest
+ * and the smallest bucket capacity that reach its occupancy, on the batch's
+ * own workload (an evaluation pass, nothing recorded), times the three fastest
  * again in three interleaved rounds and keeps the one with the best round;
  * returns it and its sampling-kernel milliseconds. */
 vegas_status vegas_batch_autotune(vegas_batch* batch, int* threads, int* rounds, double* ms);

@@ -393,6 +393,7 @@ struct vegas_batch {
   int sm_count = 0;
   // launch shape
   int threads = 256, rounds = 32, ctas = 0, cap = 16, ppt = 1, occ = 0;
+  bool small_cap = false;  // tile capacity policy (gv::choose_tile)
   size_t smem = 0;
   const void* kernel = nullptr;
   // host copies of the tables
@@ -529,7 +530,7 @@ vegas_status configure(vegas_batch* b) {
   };
   int occ_cap = 0;
   BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, b->kernel, b->threads, 0));
-  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, 1, occ_cap, occ_of);
+  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, 1, occ_cap, occ_of, b->small_cap);
   BK(b, e);
   if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
   b->smem = batch_smem(b->prec, b->N, t.cap);
@@ -890,11 +891,14 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   static const int kRounds[] = {8, 16, 32, 64, 128};
   struct Cand {
     int t, r;
+    bool small;
     double ms;
   };
   std::vector<Cand> cands;
-  // one warm-up pass, then the mean of n passes, for shape (t, r)
-  auto time_shape = [&](int t, int r, int n, double* out) -> vegas_status {
+  // one warm-up pass, then the mean of n passes, for shape (t, r) and
+  // capacity policy `small`
+  auto time_shape = [&](int t, int r, bool small, int n, double* out) -> vegas_status {
+    b->small_cap = small;
     vegas_status st = vegas_batch_set_launch(b, t, r);
     double m[2];
     if (!st) st = vegas_batch_profile(b, 1, m);
@@ -904,10 +908,15 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   };
   for (int t : kThreads)
     for (int r : kRounds) {
-      double m = 0.0;
-      vegas_status st = time_shape(t, r, 3, &m);
-      if (st) return st;
-      cands.push_back({t, r, m});
+      int cap_large = -1;  // a repeated tile is not timed twice
+      for (bool small : {false, true}) {
+        double m = 0.0;
+        vegas_status st = time_shape(t, r, small, 3, &m);
+        if (st) return st;
+        if (small && b->cap == cap_large) continue;
+        if (!small) cap_large = b->cap;
+        cands.push_back({t, r, small, m});
+      }
     }
   // the three fastest again in interleaved rounds, keeping each one's best
   std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
@@ -915,12 +924,13 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   for (int k = 0; k < 3; ++k)
     for (Cand& c : cands) {
       double m = 0.0;
-      vegas_status st = time_shape(c.t, c.r, 3, &m);
+      vegas_status st = time_shape(c.t, c.r, c.small, 3, &m);
       if (st) return st;
       c.ms = k == 0 ? m : std::min(c.ms, m);
     }
   const Cand best = *std::min_element(cands.begin(), cands.end(),
                                       [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
+  b->small_cap = best.small;
   vegas_status st = vegas_batch_set_launch(b, best.t, best.r);
   if (st) return st;
   if (threads) *threads = best.t;
