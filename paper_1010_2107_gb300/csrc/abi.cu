@@ -462,7 +462,7 @@ gv::FinArgs fin_args(const vegas_ctx* c, int refine, int record, bool nobins = f
   F.pair32 = c->prec == VG_FP32_ACCCOMP;
   F.ncall = (uint64_t)c->cfg.ncall;
   F.ncubes = c->ncubes;
-  F.scale = c->scale;
+  F.scale = c->d_derived + gv::kNumDerived;
   F.alpha = c->cfg.alpha;
   F.part_bins = c->d_part_bins;
   F.part_tot = c->d_part_tot;
@@ -580,11 +580,13 @@ vegas_status upload_grid(vegas_ctx* c, const double* edges) {
 }
 
 vegas_status upload_derived(vegas_ctx* c) {
-  vegas_status st = stage(c, gv::kNumDerived);
+  vegas_status st = stage(c, gv::kNumDerived + 1);
   if (st) return st;
   CK(c, cudaStreamSynchronize(c->stream));
   memcpy(c->h_stage, c->derived, sizeof c->derived);
-  CK(c, cudaMemcpyAsync(c->d_derived, c->h_stage, sizeof c->derived, cudaMemcpyHostToDevice, c->stream));
+  c->h_stage[gv::kNumDerived] = c->scale;  // the output scale follows the constants
+  CK(c, cudaMemcpyAsync(c->d_derived, c->h_stage, sizeof c->derived + sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return VEGAS_OK;
 }
@@ -690,7 +692,7 @@ vegas_status finish_create(vegas_ctx* c, vegas_ctx** out) {
   if (!st) st = alloc((void**)&c->d_edges, sizeof(double) * d * (N + 1));
   if (!st) st = alloc((void**)&c->d_tab64, sizeof(double2) * d * N);
   if (!st) st = alloc((void**)&c->d_tab32, sizeof(float2) * d * N);
-  if (!st) st = alloc((void**)&c->d_derived, sizeof c->derived);
+  if (!st) st = alloc((void**)&c->d_derived, sizeof c->derived + sizeof(double));  // + the output scale
   if (!st) st = alloc((void**)&c->d_bins, sizeof(double) * 2 * d * N);
   if (!st) st = alloc((void**)&c->d_tot, sizeof(double) * gv::kTotCols);
   if (!st && c->strat) st = alloc((void**)&c->d_cubes, sizeof(double) * 2 * G);
@@ -1143,7 +1145,8 @@ vegas_status vegas_set_params(vegas_ctx* c, const double* params, int nparams) {
   c->params = p;
   memcpy(c->derived, dv, sizeof dv);
   c->scale = sc;
-  destroy_graphs(c);  // the scale is baked into the captured kernels
+  // constants and scale live in device memory: the captured graphs read
+  // them at run time and stay valid
   return upload_derived(c);
 }
 
@@ -1455,11 +1458,11 @@ unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 int g_noalloc_sms[kNoAllocMaxDevices] = {};
 
 struct DerivedBlock {
-  double v[gv::kNumDerived];
+  double v[gv::kNumDerived + 1];  // the constants, then the output scale
 };
 
 __global__ void k_noalloc_params(DerivedBlock b, double* dst) {
-  for (int i = threadIdx.x; i < gv::kNumDerived; i += blockDim.x) dst[i] = b.v[i];
+  for (int i = threadIdx.x; i <= gv::kNumDerived; i += blockDim.x) dst[i] = b.v[i];
 }
 
 __global__ void k_noalloc_result(const GState* st, double* out) {
@@ -1512,6 +1515,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
       snprintf(why_buf, sizeof why_buf, "%s", why.c_str());
       return thread_fail(VEGAS_EINVAL, "%s", why_buf);
     }
+    db.v[gv::kNumDerived] = scale;
   }
   gv::KernelEntry ke{};
   if (!lookup_kernel(fn->kind, cfg->precision, ybits, d, &ke))
@@ -1569,7 +1573,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   const int dN = d * N;
   const size_t off_st = 0;
   const size_t off_dp = align256(off_st + sizeof(GState));
-  const size_t off_t64 = align256(off_dp + sizeof(double) * gv::kNumDerived);
+  const size_t off_t64 = align256(off_dp + sizeof(double) * (gv::kNumDerived + 1));
   const size_t off_t32 = align256(off_t64 + sizeof(double2) * dN);
   const size_t off_tot = align256(off_t32 + sizeof(float2) * dN);
   const size_t off_rows = align256(off_tot + sizeof(double) * gv::kTotCols);
@@ -1652,7 +1656,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   F.pair32 = cfg->precision == VG_FP32_ACCCOMP;
   F.ncall = (uint64_t)cfg->ncall;
   F.ncubes = G;
-  F.scale = scale;
+  F.scale = reinterpret_cast<double*>(scratch + off_dp) + gv::kNumDerived;
   F.alpha = cfg->alpha;
   F.part_bins = part_bins;
   F.part_tot = part_tot;

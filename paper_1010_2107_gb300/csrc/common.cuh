@@ -256,7 +256,8 @@ struct FinArgs {
   int pair32;              // part_bins hold float (hi, lo) pairs
   uint64_t ncall;
   uint64_t ncubes;
-  double scale;            // integrand output scale (RAMBO units)
+  const double* scale;     // integrand output scale (RAMBO units), in device memory so
+                           // that captured graphs follow vegas_set_params
   double alpha;
   const void* part_bins;
   const double* part_tot;

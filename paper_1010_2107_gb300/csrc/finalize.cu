@@ -149,13 +149,15 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(const FinArgs F) {
     if (i < 2 * N) {
       const int col = i < N ? a * N + i : dN + a * N + (i - N);
       const double v = column_sum(F, col, lane);
-      if (lane == 0) F.bins[col] = v * (i < N ? F.scale : F.scale * F.scale);
+      const double sc = *F.scale;
+      if (lane == 0) F.bins[col] = v * (i < N ? sc : sc * sc);
     }
   } else if (warp < kTotCols) {
     const int q = warp;
     if (q < 5) {
       const double v = column_sum(F, 2 * dN + q, lane);
-      const double sc = (q == TOT_SW || q == TOT_SI) ? F.scale : (q == TOT_NONFINITE ? 1.0 : F.scale * F.scale);
+      const double s1 = *F.scale;
+      const double sc = (q == TOT_SW || q == TOT_SI) ? s1 : (q == TOT_NONFINITE ? 1.0 : s1 * s1);
       if (lane == 0) F.tot[q] = v * sc;
     }
   }

@@ -351,3 +351,25 @@ def test_frozen_grid_passes_skip_only_the_bin_sums(gv, orc, precision, nstrat, n
     tol = 1e-13 if precision == 0 else 1e-6
     np.testing.assert_allclose(hist[:, 0], ev[:, 0], rtol=tol)
     np.testing.assert_allclose(hist[:, 1], ev[:, 1], rtol=1e3 * tol)
+
+
+def test_set_params_reaches_captured_graphs(gv):
+    """The integrand constants and the output scale live in device memory, so
+    a graph captured before vegas_set_params computes with the new values
+    (the RAMBO scale changes with sqrt(s)): same results as a fresh context."""
+    p1, p2 = wl.rambo_params(3, sqrt_s=500.0), wl.rambo_params(3, sqrt_s=900.0)
+    kw = dict(ncall=20000, precision=0, ybits=53, seed=4)
+    with gv.vegas_create(wl.RAMBO_BW, 12, p1, **kw) as a, gv.vegas_create(wl.RAMBO_BW, 12, p2, **kw) as b:
+        gv.vegas_iterate(a, 2, refine=True)  # captures the graph with p1
+        gv.vegas_reset_grid(a)
+        gv.vegas_reset_results(a)
+        gv.vegas_set_iteration(a, 0)
+        gv.vegas_set_params(a, p2)
+        ra = gv.vegas_iterate(a, 2, refine=True)  # same call shape: the cached graph
+        rb = gv.vegas_iterate(b, 2, refine=True)
+        # equal up to the order of the shared-memory bucket claims, which
+        # moves the last bits of the per-bin sums and through refinement the
+        # second iteration (a stale scale would be off by (9/5)^k)
+        assert ra["I"] == pytest.approx(rb["I"], rel=1e-12)
+        assert ra["sigma"] == pytest.approx(rb["sigma"], rel=1e-9)
+        np.testing.assert_allclose(gv.vegas_get_grid(a), gv.vegas_get_grid(b), rtol=0, atol=1e-12)
