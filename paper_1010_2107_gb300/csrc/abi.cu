@@ -558,6 +558,7 @@ void fill_result(const vegas_ctx* c, vegas_result* r) {
 
 vegas_status stage(vegas_ctx* c, size_t n) {
   if (n <= c->h_stage_len) return VEGAS_OK;
+  CK(c, cudaStreamSynchronize(c->stream));  // no copy may still read the old buffer
   if (c->h_stage) cudaFreeHost(c->h_stage);
   c->h_stage = nullptr;
   c->h_stage_len = 0;
@@ -575,8 +576,7 @@ vegas_status upload_grid(vegas_ctx* c, const double* edges) {
   memcpy(c->h_stage, edges, n * sizeof(double));
   CK(c, cudaMemcpyAsync(c->d_edges, c->h_stage, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(c, gv_launch_tables(c->d_edges, d, N, c->d_tab64, c->d_tab32, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  return VEGAS_OK;
+  return VEGAS_OK;  // stream-ordered; the next host write to the stage synchronises first
 }
 
 vegas_status upload_derived(vegas_ctx* c) {
@@ -587,8 +587,7 @@ vegas_status upload_derived(vegas_ctx* c) {
   c->h_stage[gv::kNumDerived] = c->scale;  // the output scale follows the constants
   CK(c, cudaMemcpyAsync(c->d_derived, c->h_stage, sizeof c->derived + sizeof(double), cudaMemcpyHostToDevice,
                         c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  return VEGAS_OK;
+  return VEGAS_OK;  // stream-ordered; the next host write to the stage synchronises first
 }
 
 bool valid_grid(const double* e, int d, int N) {
