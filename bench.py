@@ -402,6 +402,11 @@ class Runner:
         if self.mode == "adjoint":  # the grid the gradient is taken on
             gv.vegas_iterate(h, w["warmup_iters"], refine=True)
         elif self.mode == "spring":  # the BASES run whose integration phase bounds the cubes
+            import numpy as np
+            import torch
+            n = w["ntrials"]  # pinned event buffers for the end-to-end steps, made once
+            self._pinned = (torch.empty((n, w["ndim"]), dtype=torch.float64, pin_memory=True).numpy(),
+                            torch.empty(n, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64))
             if self.autotune:
                 tuned = gv.vegas_autotune(h)
                 self.tuned = self.tuned or tuned
@@ -544,8 +549,8 @@ class Runner:
             gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=True)
             return 0, 48 * len(self.insts) + 1200 * len(self.insts)
         d, N = w["ndim"], w["nbins"]
-        if self.mode == "spring":  # events copied to host memory; the frozen grid stays
-            r = gv.spring_generate(h, 0, w["ntrials"], events=True)
+        if self.mode == "spring":  # events copied to pinned host memory; the frozen grid stays
+            r = gv.spring_generate(h, 0, w["ntrials"], events=True, out_x=self._pinned[0], out_t=self._pinned[1])
             return 0, r["n_events"] * (8 * d + 8)
         edges0 = np.tile(np.arange(N + 1, dtype=np.float64) / N, (d, 1))
         gv.vegas_set_grid(h, edges0)

@@ -351,12 +351,20 @@ def vegas_get_cube_max(ctx: Context):
     return out
 
 
-def spring_generate(ctx: Context, trial0: int, n_trials: int, events: bool = True):
+def spring_generate(ctx: Context, trial0: int, n_trials: int, events: bool = True, out_x=None, out_t=None):
     """SPRING trials trial0 .. trial0 + n_trials - 1; returns the kept points
-    (host copies when `events`), their trial indices, and the counts."""
+    (host copies when `events`), their trial indices, and the counts.
+    out_x ([n_trials][ndim] float64) and out_t ([n_trials] uint64) may be
+    given, e.g. in pinned memory; the results are views of their heads."""
     n_ev, n_ov, n_np = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
-    x = np.zeros((n_trials, ctx.ndim)) if events else None
-    t = np.zeros(n_trials, dtype=np.uint64) if events else None
+    x = t = None
+    if events:
+        x = out_x if out_x is not None else np.empty((n_trials, ctx.ndim))
+        t = out_t if out_t is not None else np.empty(n_trials, dtype=np.uint64)
+        if x.shape != (n_trials, ctx.ndim) or x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("out_x must be a C-contiguous float64 array [n_trials][ndim]")
+        if t.shape != (n_trials,) or t.dtype != np.uint64 or not t.flags.c_contiguous:
+            raise ValueError("out_t must be a C-contiguous uint64 array [n_trials]")
     _check(lib().spring_generate(ctx.handle, int(trial0), int(n_trials), _dp(x) if events else None,
                                  t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if events else None,
                                  ctypes.byref(n_ev), ctypes.byref(n_ov), ctypes.byref(n_np)), ctx.handle)
