@@ -99,3 +99,31 @@ def test_null_arguments(gvlib):
     assert L.bases_integrate(None, 1, 0.0, 1, 0.0, None, None) == gv.EINVAL
     L.vegas_destroy(None)
     assert isinstance(gv.vegas_last_error(None), str)
+
+
+@pytest.mark.parametrize("kind,ndim,params", [
+    (8, 5, None),          # W -> mu nu: a single-context workload
+    (5, 8, None),          # RAMBO
+    (64, 4, [1.0, 2.0]),   # run-time compiled kinds have no batched kernel
+])
+def test_batch_rejects_unbatched_kinds(gvlib, kind, ndim, params):
+    gv = gvlib
+    import numpy as np
+    from paper_1010_2107_gb300 import workloads as wl
+    if params is None:
+        params = wl.w_munu_params() if kind == 8 else wl.rambo_params(2)
+    with pytest.raises(gv.VegasError) as e:
+        gv.vegas_batch_create([dict(kind=kind, ndim=ndim, ncall=1000, params=np.asarray(params, float))])
+    assert e.value.status == gv.EINVAL
+
+
+def test_user_kind_needs_its_own_constructor(gvlib):
+    gv = gvlib
+    import numpy as np
+    with pytest.raises(gv.VegasError) as e:
+        gv.vegas_create(gv.USER, 4, np.ones(3))
+    assert e.value.status == gv.EINVAL and "kind" in str(e.value)
+    with pytest.raises(gv.VegasError) as e:
+        gv.vegas_create_user("template <typename T> __device__ T vegas_user_f(const T* x, int d, const T* p)"
+                             " { return x[0]; }", 4, np.ones(gv.MAXUSERPARAMS + 1))
+    assert e.value.status == gv.EINVAL
