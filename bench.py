@@ -446,8 +446,8 @@ class Runner:
             return 2 + 2 + 2 * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return 2
-        if self.mode == "spring":  # cube table (4 kernels), trials, compaction
-            return 6
+        if self.mode == "spring":  # cube table and guide (5 kernels), trials, compaction
+            return 7
         return 2 + 2 + 2 * w["itmx"]
 
     def step(self, h):

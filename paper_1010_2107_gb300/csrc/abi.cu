@@ -85,7 +85,7 @@ struct vegas_ctx {
   uint64_t* d_prefix = nullptr;
   double* d_mt = nullptr;          // [G] cube bounds q_c / scale
   float* d_mt32 = nullptr;         // [G] the same in FP32
-  uint64_t* d_psample = nullptr;   // sampled prefix sums (first level of the cube search)
+  uint32_t* d_guide = nullptr;     // guide table of the cube search
   double* d_bmax = nullptr;        // per-block maxima and sums of the table kernels
   unsigned long long* d_bsum = nullptr;
   double* d_meta = nullptr;        // {Q, scale, status}
@@ -184,8 +184,10 @@ void destroy_graphs(vegas_ctx* c) {
 //   k_spring_scan     (one block) exclusive scan of the block sums,
 //                     P[G] = Q, meta = {Q, scale, status} (status 1: no
 //                     positive maximum);
-//   k_spring_prefix   exclusive prefix sums P[0..G) in 64-bit integers and
-//                     their sample psample[j] = P[j 2^psh].
+//   k_spring_prefix   exclusive prefix sums P[0..G) in 64-bit integers;
+//   k_spring_guide    the guide table (Chen and Asau): for each of the 2^gk
+//                     equal intervals of [0, Q), guide[j] = the last cube c
+//                     with P[c] <= floor(j Q / 2^gk); guide[2^gk] = G - 1.
 constexpr int kSpanThreads = 256, kSpanPer = 4;
 constexpr uint32_t kSpan = kSpanThreads * kSpanPer;  // cubes per block
 
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_spring_scan(const double* bmax, uint32
 
 __global__ void __launch_bounds__(kSpanThreads) k_spring_prefix(const uint64_t* q, uint32_t G,
                                                                 const unsigned long long* boff, uint64_t* prefix,
-                                                                uint64_t* psample, uint32_t psh, const double* meta) {
+                                                                const double* meta) {
   __shared__ unsigned long long sw[32];
   if (meta[2] != 0.0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -310,16 +312,34 @@ __global__ void __launch_bounds__(kSpanThreads) k_spring_prefix(const uint64_t* 
   __syncthreads();
   unsigned long long run = boff[blockIdx.x] + inc - s;
   for (int w = 0; w < warp; ++w) run += sw[w];
-  const uint32_t smask = (1u << psh) - 1u;
 #pragma unroll
   for (int k = 0; k < kSpanPer; ++k) {
     const uint32_t i = lo + k;
-    if (i < G) {
-      prefix[i] = run;
-      if ((i & smask) == 0) psample[i >> psh] = run;
-    }
+    if (i < G) prefix[i] = run;
     run += v[k];
   }
+}
+
+// One guide entry per thread: the interval start b_j = floor(j Q / 2^gk)
+// from the 128-bit product, then the last cube with P[c] <= b_j by
+// bisection (P[0] = 0 <= b_j always).
+__global__ void __launch_bounds__(256) k_spring_guide(const uint64_t* prefix, uint32_t G, uint32_t gk,
+                                                      uint32_t* guide, const double* meta) {
+  if (meta[2] != 0.0) return;
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > (1u << gk)) return;
+  const uint64_t Q = prefix[G];
+  const uint64_t plo = (uint64_t)j * Q, phi = __umul64hi((uint64_t)j, Q);
+  const uint64_t b = gk ? ((phi << (64 - gk)) | (plo >> gk)) : plo;
+  uint32_t lo = 0, hi = G;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (prefix[mid] <= b)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  guide[j] = lo;
 }
 
 // SPRING compaction: block k copies chunk k's kept points behind those of
@@ -749,7 +769,7 @@ void vegas_destroy(vegas_ctx* c) {
   cudaFree(c->d_tot);
   cudaFree(c->d_cubes);
   cudaFree(c->d_cube_max);
-  for (void* p : {(void*)c->d_q, (void*)c->d_mt, (void*)c->d_mt32, (void*)c->d_psample, (void*)c->d_bmax, (void*)c->d_bsum, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
+  for (void* p : {(void*)c->d_q, (void*)c->d_mt, (void*)c->d_mt32, (void*)c->d_guide, (void*)c->d_bmax, (void*)c->d_bsum, (void*)c->d_prefix, (void*)c->d_meta, (void*)c->d_stage_x, (void*)c->d_stage_t,
                   (void*)c->d_out_x, (void*)c->d_out_t, (void*)c->d_counts, (void*)c->d_counters})
     cudaFree(p);
   cudaFree(c->d_gpart);
@@ -988,14 +1008,13 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
     return VEGAS_OK;
   };
   vegas_status st = VEGAS_OK;
-  uint32_t psh = 0;  // sample stride 2^psh: at most 4096 sampled prefixes (32 KB) per CTA
-  while ((c->ncubes + (1ull << psh) - 1) >> psh > 4096) ++psh;
-  const uint32_t nsample = (uint32_t)((c->ncubes + (1ull << psh) - 1) >> psh);
+  uint32_t gk = 0;  // 2^gk guide intervals: about one per cube, at most 2^22 (16 MB)
+  while (gk < 22 && (1ull << gk) < c->ncubes) ++gk;
   if (!c->d_q) {
     if (!st) st = grow((void**)&c->d_q, sizeof(uint64_t) * c->ncubes);
     if (!st) st = grow((void**)&c->d_mt, sizeof(double) * c->ncubes);
     if (!st) st = grow((void**)&c->d_mt32, sizeof(float) * c->ncubes);
-    if (!st) st = grow((void**)&c->d_psample, sizeof(uint64_t) * nsample);
+    if (!st) st = grow((void**)&c->d_guide, sizeof(uint32_t) * ((1ull << gk) + 1));
     const size_t nb = (c->ncubes + kSpan - 1) / kSpan;
     if (!st) st = grow((void**)&c->d_bmax, sizeof(double) * nb);
     if (!st) st = grow((void**)&c->d_bsum, sizeof(unsigned long long) * nb);
@@ -1025,8 +1044,9 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
     k_spring_weights<<<nb, kSpanThreads, 0, c->stream>>>(c->d_cube_max, G, c->scale, c->d_bmax, nb, c->d_q,
                                                          c->d_mt, c->d_mt32, c->d_bsum);
     k_spring_scan<<<1, 1024, 0, c->stream>>>(c->d_bmax, nb, c->d_bsum, G, c->d_prefix, c->d_meta);
-    k_spring_prefix<<<nb, kSpanThreads, 0, c->stream>>>(c->d_q, G, c->d_bsum, c->d_prefix, c->d_psample, psh,
-                                                        c->d_meta);
+    k_spring_prefix<<<nb, kSpanThreads, 0, c->stream>>>(c->d_q, G, c->d_bsum, c->d_prefix, c->d_meta);
+    k_spring_guide<<<(uint32_t)(((1ull << gk) + 256) / 256), 256, 0, c->stream>>>(c->d_prefix, G, gk, c->d_guide,
+                                                                                  c->d_meta);
   }
   CK(c, cudaGetLastError());
   CK(c, cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 2, c->stream));
@@ -1035,9 +1055,8 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   R.prefix = c->d_prefix;
   R.mt = c->d_mt;
   R.mt32 = c->d_mt32;
-  R.psample = c->d_psample;
-  R.nsample = nsample;
-  R.psh = psh;
+  R.guide = c->d_guide;
+  R.gk = gk;
   R.meta = c->d_meta;
   R.out_scale = c->scale;
   R.trial0 = (uint32_t)trial0;
@@ -1049,9 +1068,8 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   R.counts = c->d_counts;
   R.counters = c->d_counters;
   const bool f64 = c->prec == VG_FP64;
-  const size_t smem = gv::spring_sample_offset(d * N, f64 ? sizeof(double2) : sizeof(float2),
-                                               f64 ? sizeof(double) : sizeof(float)) +
-                      sizeof(uint64_t) * nsample;
+  const size_t smem = (size_t)d * N * (f64 ? sizeof(double2) : sizeof(float2)) +
+                      gv::kNumDerived * (f64 ? sizeof(double) : sizeof(float));
   int occ = 0;
   CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem));

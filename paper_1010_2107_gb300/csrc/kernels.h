@@ -158,8 +158,9 @@ struct SpringArgs {
   const uint64_t* prefix;   // [G + 1] exclusive prefix sums of the integer cube weights
   const double* mt;         // [G] cube bounds q_c / scale (FP64, formed by the table kernel)
   const float* mt32;        // [G] the same rounded to FP32 (the FP32 kernels' keep decision)
-  const uint64_t* psample;  // [nsample] prefix[j << psh]: the first level of the cube search
-  uint32_t nsample, psh;    // nsample = ceil(G / 2^psh) (staged in shared memory)
+  const uint32_t* guide;    // [2^gk + 1] guide table of the cube search (Chen and Asau):
+                            // guide[j] = the last cube c with prefix[c] <= floor(j Q / 2^gk)
+  uint32_t gk;              // log2 of the number of guide intervals
   const double* meta;       // {Q, scale} written by the table kernel
   double out_scale;         // integrand output scale: weights in the integrand's units
   uint32_t trial0, n, chunk, nchunks;
@@ -168,12 +169,6 @@ struct SpringArgs {
   uint32_t* counts;
   unsigned long long* counters;
 };
-
-// Byte offset of the sampled prefix table in the SPRING kernel's shared
-// memory: after the grid table (dN cells) and the constants, 8-aligned.
-__host__ __device__ inline size_t spring_sample_offset(int dN, size_t cell, size_t scalar) {
-  return ((size_t)dN * cell + (size_t)kNumDerived * scalar + 7) & ~(size_t)7;
-}
 
 // Arguments of the per-sample dump kernel.
 struct DumpArgs {

@@ -724,17 +724,14 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + (size_t)dN * sizeof(T2));
-  uint64_t* ps = reinterpret_cast<uint64_t*>(smem + spring_sample_offset(dN, sizeof(T2), sizeof(T)));
   __shared__ uint32_t wcount[8];
   __shared__ uint32_t chunk_count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
   for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)A.dparams[i];
-  for (uint32_t i = tid; i < R.nsample; i += blockDim.x) ps[i] = R.psample[i];
   __syncthreads();
-  const double Q = R.meta[0];
-  const uint64_t Qi = (uint64_t)Q;
+  const uint64_t Qi = R.prefix[A.ncubes];  // Q, the total integer weight
   const uint32_t G = A.ncubes;
   const int W = YB == 24 ? d : 2 * d;
   // words W .. W+2 (24-bit) or W+3 (53-bit) from the blocks of W >> 2 on:
@@ -762,18 +759,11 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
         const uint64_t U = ((uint64_t)wx[o] << 32) | (uint64_t)wx[o + 1];
         const uint64_t u = __umul64hi(U, Qi);
         // the cube c with prefix[c] <= u < prefix[c + 1] (the last of equal
-        // prefixes): bisection over the shared-memory sample prefix[j << psh],
-        // then over the 2^psh cubes of the chosen stretch in global memory
-        uint32_t lo = 0, hi = R.nsample;
-        while (hi - lo > 1) {
-          const uint32_t mid = lo + ((hi - lo) >> 1);
-          if (ps[mid] <= u)
-            lo = mid;
-          else
-            hi = mid;
-        }
-        lo <<= R.psh;
-        hi = min(lo + (1u << R.psh), G);
+        // prefixes).  u lies in guide interval j = floor(U 2^gk / 2^64), whose
+        // ends floor(j Q / 2^gk) and floor((j + 1) Q / 2^gk) bound it, so c
+        // lies in [guide[j], guide[j + 1]]: a bisection over those cubes only
+        const uint32_t j = R.gk ? (uint32_t)(U >> (64 - R.gk)) : 0u;
+        uint32_t lo = __ldg(R.guide + j), hi = __ldg(R.guide + j + 1) + 1u;
         while (hi - lo > 1) {
           const uint32_t mid = lo + ((hi - lo) >> 1);
           if (__ldg(R.prefix + mid) <= u)
