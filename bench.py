@@ -63,8 +63,8 @@ ALGO_OPS = {
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/), per pass kind (refining, frozen grid); a workload
 # whose kernel changed since its capture has no entry.
-TRAFFIC = {"dgauss8": (81152, 612608), "wmunu": (79104, 350976), "spring_dgauss8": (705536 + 4038144,),
-           "rambo4_adjoint": (1298688,)}
+TRAFFIC = {"dgauss8": (81152, 612608), "wmunu": (79104, 350976), "rambo4_adjoint": (1298688,),
+           "spring_dgauss8": (1010688 + 4200960,)}
 
 
 def _workload(name):
