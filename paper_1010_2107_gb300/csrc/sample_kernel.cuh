@@ -724,8 +724,11 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
   T* P = reinterpret_cast<T*>(smem + (size_t)dN * sizeof(T2));
-  __shared__ uint32_t wcount[8];
-  __shared__ uint32_t chunk_count;
+  // kept trials per warp, double-buffered by round: one barrier per round
+  // (a buffer is rewritten two rounds later, after every thread has passed
+  // the next round's barrier)
+  __shared__ uint32_t wcount[2][8];
+  uint32_t parity = 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const T2* gtab = reinterpret_cast<const T2*>(A.tab);
   for (int i = tid; i < dN; i += blockDim.x) tab[i] = gtab[i];
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
   const bool two_blocks = o + (YB == 24 ? 3 : 4) > 4;
   unsigned long long ov = 0, np = 0;
   for (uint32_t chunk = blockIdx.x; chunk < R.nchunks; chunk += gridDim.x) {
-    if (tid == 0) chunk_count = 0;
+    uint32_t chunk_count = 0;  // the same in every thread
     const uint32_t base = chunk * R.chunk;
     for (uint32_t r = 0; r < R.chunk; r += blockDim.x) {
       const uint32_t rel = base + r + tid;
@@ -823,13 +826,14 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
         }
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) wcount[warp] = __popc(bal);
+      if (lane == 0) wcount[parity][warp] = __popc(bal);
       __syncthreads();
       uint32_t off = chunk_count, tot = 0;
       for (int k = 0; k < nw; ++k) {
-        if (k < warp) off += wcount[k];
-        tot += wcount[k];
+        if (k < warp) off += wcount[parity][k];
+        tot += wcount[parity][k];
       }
+      parity ^= 1u;
       if (keep) {
         const uint32_t pos = base + off + __popc(bal & ((1u << lane) - 1u));
 #pragma unroll
@@ -837,12 +841,9 @@ __global__ void __launch_bounds__(256) k_spring(const SpringArgs R) {
           if (a < d) R.stage_x[(size_t)pos * d + a] = (double)x[a];
         R.stage_t[pos] = (uint64_t)R.trial0 + rel;
       }
-      __syncthreads();
-      if (tid == 0) chunk_count += tot;
-      __syncthreads();
+      chunk_count += tot;
     }
     if (tid == 0) R.counts[chunk] = chunk_count;
-    __syncthreads();
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
