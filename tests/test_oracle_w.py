@@ -148,3 +148,11 @@ def test_one_helicity_and_no_azimuth():
     y2 = y.copy()
     y2[:, 3] = rng.random(len(y))
     np.testing.assert_array_equal(_f(p, y2), f)
+
+
+def test_wrong_dimension_or_parameter_count_is_rejected():
+    p = wl.w_munu_params()
+    with pytest.raises(ValueError):
+        oracle.integrand(oracle.Integrand(oracle.W_MUNU, 4, p), np.full((1, 4), 0.5))
+    with pytest.raises(ValueError):
+        oracle.integrand(oracle.Integrand(oracle.W_MUNU, 5, p[:-1]), np.full((1, 5), 0.5))

@@ -57,3 +57,14 @@ def test_bad_shapes_are_rejected_before_compiling(gv):
         with pytest.raises(gv.VegasError) as e:
             gv.vegas_user_compile(GAUSS, d, **kw)
         assert e.value.status == gv.EINVAL
+
+
+def test_library_helpers_are_visible_to_user_code(gv):
+    """The embedded kernel headers come with their device helpers (namespace
+    gv): the benchmarked two-peak Gaussian source uses gv::gexp."""
+    from paper_1010_2107_gb300 import workloads as wl
+    gv.vegas_user_compile(wl.DGAUSS_USER_SOURCE, 8, ncall=4 ** 8 * 2, nstrat=4, precision=2, ybits=24)
+    src = ("template <typename T> __device__ T vegas_user_f(const T* x, int d, const T* p) "
+           "{ return gv::qsqrt(x[0]) * gv::vexp(-x[1]); }")
+    for precision in (0, 2):
+        gv.vegas_user_compile(src, 2, precision=precision)
