@@ -13,7 +13,8 @@
  * Neumaier-compensated sums; no blocking, fusion or reordering beyond the
  * order of the steps.
  *
- * Parity unpinned: the full RAMBO integrand with cuts (see oracle.h).
+ * Parity unpinned: the full RAMBO integrand with cuts for n >= 3 partons
+ * (see oracle.h).
  */
 #include "oracle.h"
 

@@ -15,10 +15,12 @@
  * x86-64 and aarch64 give identical results.
  *
  * Parity unpinned: the full RAMBO integrand with its cuts (kind 5, obs 0)
- * has no closed form.  Its building blocks are pinned (phase-space volume,
- * momentum conservation, <s12>, the s12 density, hand-built cut cases and
- * Lorentz / azimuthal invariances) but the complete product is checked
- * only against the CUDA path and by statistical consistency.
+ * for n >= 3 partons has no closed form.  Its building blocks are pinned
+ * (phase-space volume, momentum conservation, <s12>, the s12 density,
+ * hand-built cut cases and Lorentz / azimuthal invariances) and so is the
+ * complete product for n = 2, with both cut forms, against its closed
+ * form; for n >= 3 the product is checked only against the CUDA path and
+ * by statistical consistency.
  */
 #ifndef GVEGAS_ORACLE_H
 #define GVEGAS_ORACLE_H

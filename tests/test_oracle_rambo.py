@@ -203,3 +203,29 @@ def test_zero_random_number_gives_zero_weight(orc):
     x = np.full(4 * n, 0.5)
     x[4] = 0.0
     assert orc.integrand(_fn(orc, n, cut=2), x)[0] == 0.0
+
+
+@pytest.mark.parametrize("cut", [0, 1])
+def test_two_body_integrand_against_its_closed_form(orc, cut):
+    """n = 2 pins the whole RAMBO integrand, cuts included: the partons are
+    back to back with s12 = s21 = s and cos(theta) uniform, so
+    f = V_2 cut BW(s) / s^2 with V_2 = pi/2, both transverse momenta equal
+    (sqrt(s)/2) sin(theta), and Delta R >= pi passes any Delta R cut.  Hard
+    cut: the mean of the cut is sqrt(1 - (2 ptmin / sqrt s)^2); sigmoid cut:
+    the mean of sigmoid((pT - T)/w)^2 over cos(theta), by quadrature."""
+    from scipy import integrate
+    s = SQRTS ** 2
+    p = wl.rambo_params(2, cut=cut, ptmin=150.0, T=150.0, wc=20.0)
+    M, G = p[wl.RB_M], p[wl.RB_GAMMA]
+    bw = M * G / ((s - M * M) ** 2 + M * M * G * G)
+    if cut == 0:
+        acc = math.sqrt(1.0 - (2.0 * p[wl.RB_PTMIN] / SQRTS) ** 2)
+    else:
+        sig = lambda c: 1.0 / (1.0 + math.exp(-((SQRTS / 2) * math.sqrt(1 - c * c) - p[wl.RB_T]) / p[wl.RB_WC]))
+        acc = 0.5 * integrate.quad(lambda c: sig(c) ** 2, -1.0, 1.0, epsabs=0, epsrel=1e-12, limit=200)[0]
+    expect = math.pi / 2 * bw / s ** 2 * acc
+    fn = orc.Integrand(orc.RAMBO_BW, 8, p)
+    cfg = orc.make_cfg(8, nbins=50, ncall=1 << 18, ybits=53, seed=11)
+    r = orc.iteration(cfg, fn, orc.uniform_grid(8, 50), 0)
+    assert abs(r["I"] - expect) < 5.0 * math.sqrt(r["var"])
+    assert math.sqrt(r["var"]) < 0.01 * expect
