@@ -373,3 +373,24 @@ def test_set_params_reaches_captured_graphs(gv):
         assert ra["I"] == pytest.approx(rb["I"], rel=1e-12)
         assert ra["sigma"] == pytest.approx(rb["sigma"], rel=1e-9)
         np.testing.assert_allclose(gv.vegas_get_grid(a), gv.vegas_get_grid(b), rtol=0, atol=1e-12)
+
+
+def test_two_body_rambo_fp64_matches_the_oracle(gv, orc):
+    """The two-body RAMBO integrand, whose oracle is pinned against its closed
+    form (f = V_2 cut BW(s) / s^2), in the FP64 form: the estimate to 1e-12
+    and the dumped weights point by point."""
+    p = wl.rambo_params(2, sqrt_s=1000.0, ptmin=150.0)
+    ncall = 20011
+    with gv.vegas_create(wl.RAMBO_BW, 8, p, ncall=ncall, precision=0, ybits=53) as ctx:
+        I, _ = gv.vegas_eval(ctx, 1)
+        s = np.arange(0, ncall, 7, dtype=np.uint64)
+        g = gv.vegas_sample_dump(ctx, 1, s)
+    cfg = orc.make_cfg(8, nbins=50, ncall=ncall, ybits=53)
+    fn = orc.Integrand(wl.RAMBO_BW, 8, p)
+    o = orc.iteration(cfg, fn, orc.uniform_grid(8, 50), 1)
+    ob = orc.sample_batch(cfg, orc.uniform_grid(8, 50), 1, s)
+    assert abs(I - o["I"]) <= 1e-12 * abs(o["I"])
+    assert np.array_equal(g["words"], ob["words"])
+    fo = orc.integrand(fn, ob["x"]) * ob["jac"]
+    ok = np.isclose(g["f"] * g["jac"], fo, rtol=1e-9, atol=1e-300)
+    assert np.mean(ok) >= 0.999
