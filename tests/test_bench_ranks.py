@@ -62,3 +62,22 @@ def test_single_rank_needs_no_collective():
     assert bench.max_over_ranks(3.0, None) == 3.0
     assert bench.whole_job_rate(1, 10, 2, 4.0) == 5.0
     assert bench.rank_instance(7, 0, "batched") == 7 and bench.rank_instance(0, 0, "vegas") == 0
+
+
+def test_roofline_operations_are_launch_weighted_for_bases():
+    """A BASES step launches ITMX1 refining passes (with the per-bin
+    histogram) and ITMX2 frozen-grid passes (without): the operations per
+    point are weighted by those launches; a VEGAS step counts every pass in
+    full."""
+    import bench
+    r = bench.Runner.__new__(bench.Runner)
+    r.name, r.mode = "dgauss8", "bases"
+    r.w = dict(itmx1=5, itmx2=5)
+    ops = bench.ALGO_OPS["dgauss8"]
+    full, frozen = sum(ops.values()), sum(v for k, v in ops.items() if k != "histogram")
+    assert frozen == full - ops["histogram"]
+    assert r.ops_per_point() == (5 * full + 5 * frozen) / 10
+    r.w = dict(itmx1=3, itmx2=7)
+    assert r.ops_per_point() == (3 * full + 7 * frozen) / 10
+    r.name, r.mode = "rambo5", "vegas"
+    assert r.ops_per_point() == sum(bench.ALGO_OPS["rambo5"].values())

@@ -68,3 +68,17 @@ def test_library_helpers_are_visible_to_user_code(gv):
            "{ return gv::qsqrt(x[0]) * gv::vexp(-x[1]); }")
     for precision in (0, 2):
         gv.vegas_user_compile(src, 2, precision=precision)
+
+
+def test_embedded_kernel_headers_are_current(gv):
+    """The build embeds the kernel headers in the library as text for the
+    run-time compiler; the generated table holds every header as it is on
+    disk (checked on a distinctive line of each)."""
+    import os
+    from paper_1010_2107_gb300 import _build
+    inc = open(_build.RTC_INC).read()
+    for name, path in _build.RTC_HEADERS:
+        assert '{"' + name + '",' in inc
+        lines = [l for l in open(path).read().splitlines() if len(l.strip()) > 40 and ")gvrtc" not in l]
+        assert lines and lines[len(lines) // 2] in inc, path
+    assert os.path.getmtime(_build.RTC_INC) >= max(os.path.getmtime(p) for _, p in _build.RTC_HEADERS) - 1
