@@ -270,3 +270,22 @@ def test_gradient_estimator_matches_common_random_number_differences(orc):
         Im = orc.iteration(cfg, orc.Integrand(orc.RAMBO_BW, 4 * n, pm), e, 0)["I"]
         assert g[j] == pytest.approx((Ip - Im) / (2 * h), rel=1e-3)
     assert I0 == pytest.approx(orc.iteration(cfg, orc.Integrand(orc.RAMBO_BW, 4 * n, P), e, 0)["I"], rel=1e-13)
+
+
+def test_vegas_and_bases_agree_on_the_same_integrand(orc):
+    """The paper's own check, agreement of independent methods within their
+    errors: an unstratified VEGAS run and a stratified BASES run of the same
+    integrand (disjoint Philox instances) agree within the combined sigma,
+    and both agree with the closed form."""
+    import closed_forms as cf
+    d = 3
+    p = wl.genz_gaussian_params(d, a=6.0, u=0.45)
+    fn = orc.Integrand(orc.GENZ_GAUSSIAN, d, p)
+    exact = cf.genz_gaussian(p[:d], p[d:])
+    cv = orc.make_cfg(d, nbins=50, ncall=20000, ybits=53, seed=5, instance=1)
+    rv = orc.vegas(cv, fn, orc.uniform_grid(d, 50), 0, 8)
+    cb = orc.make_cfg(d, nbins=50, ncall=4 ** d * 300, nstrat=4, ybits=53, seed=5, instance=2)
+    rb = orc.bases(cb, fn, orc.uniform_grid(d, 50), 0, 4, 0.0, 4, 0.0)
+    comb = math.sqrt(rv["sigma"] ** 2 + rb["sigma"] ** 2)
+    assert abs(rv["I"] - rb["I"]) < 4 * comb
+    assert abs(rv["I"] - exact) < 4 * rv["sigma"] and abs(rb["I"] - exact) < 4 * rb["sigma"]
