@@ -196,6 +196,16 @@ def integrand_grad(fn: Integrand, x) -> np.ndarray:
     return g
 
 
+def cut_margin(fn: Integrand, x) -> np.ndarray:
+    """Smallest relative distance of each point's cut or discontinuity
+    quantities from their edges (inf where the integrand has none)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, fn.ndim)
+    m = np.zeros(len(x))
+    if lib().orc_cut_margin(fn.fn, ctypes.c_int64(len(x)), _dp(x), _dp(m)):
+        raise ValueError("orc_cut_margin failed")
+    return m
+
+
 def rambo(n: int, sqrt_s: float, rho) -> np.ndarray:
     rho = np.ascontiguousarray(rho, dtype=np.float64)
     p = np.zeros((n, 4))

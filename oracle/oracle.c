@@ -14,7 +14,8 @@
  * order of the steps.
  *
  * Parity unpinned: the full RAMBO integrand with cuts for n >= 3 partons
- * (see oracle.h).
+ * (see oracle.h).  The cut margins (orc_cut_margin) are pinned by bisection
+ * on the integrand's own cut decisions.
  */
 #include "oracle.h"
 
@@ -527,6 +528,84 @@ int orc_integrand_grad(const orc_fn* fn, int64_t n, const double* x,
   if (nt == 0) return -1;
   for (int64_t i = 0; i < n; ++i)
     eval_point(fn, x + i * fn->ndim, grad + i * nt);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Cut margins (test infrastructure): how close each quantity that an  */
+/* integrand compares with an edge lies to that edge, as the smallest  */
+/* relative distance |q - e| / |e| over those quantities (INFINITY for */
+/* an integrand that compares none).  A point whose margin is below    */
+/* the rounding error of a computation of q may be cut on one side and */
+/* kept on the other; every other point must agree.                    */
+/* ------------------------------------------------------------------ */
+static double rel_gap(double q, double e) {
+  double den = fabs(e) > 0.0 ? fabs(e) : 1.0;
+  return fabs(q - e) / den;
+}
+
+static double margin_point(const orc_fn* fn, const double* x) {
+  const double* P = fn->params;
+  int d = fn->ndim;
+  double m = INFINITY;
+  switch (fn->kind) {
+    case ORC_GENZ_DISCONTINUOUS: {
+      const double* u = P + d;
+      m = rel_gap(x[0], u[0]);
+      if (d > 1) m = fmin(m, rel_gap(x[1], u[1]));
+      return m;
+    }
+    case ORC_W_MUNU: {
+      /* the quantities w_munu tests, in its own arithmetic */
+      const double S = P[ORC_W_SQRTS] * P[ORC_W_SQRTS], M = P[ORC_W_M], G = P[ORC_W_GAMMA];
+      const double rho_lo = atan((P[ORC_W_SMIN] - M * M) / (M * G)), rho_hi = atan((S - M * M) / (M * G));
+      const double shat = M * M + M * G * tan(rho_lo + (rho_hi - rho_lo) * x[0]);
+      const double tau = shat / S;
+      if (!(tau > 0.0 && tau < 1.0)) return rel_gap(tau, tau > 0.5 ? 1.0 : 0.0);
+      const double L = -log(tau), yw = (x[1] - 0.5) * L;
+      m = fmin(rel_gap(sqrt(tau) * exp(yw), 1.0), rel_gap(sqrt(tau) * exp(-yw), 1.0));
+      const double k = floor(16.0 * x[4] + 0.5); /* nearest helicity-cell edge */
+      if (k >= 1.0 && k <= 15.0) m = fmin(m, rel_gap(16.0 * x[4], k));
+      if (P[ORC_W_CUTS] != 0.0) {
+        const double c = 2.0 * x[2] - 1.0;
+        const double pt = 0.5 * sqrt(shat) * sqrt(1.0 - c * c);
+        const double eta = atanh(c) + yw;
+        m = fmin(m, fmin(rel_gap(pt, P[ORC_W_PTMIN]), rel_gap(fabs(eta), P[ORC_W_ETAMAX])));
+      }
+      return m;
+    }
+    case ORC_RAMBO_BW: {
+      int n = (int)P[ORC_RB_N], cut = (int)P[ORC_RB_CUT], obs = (int)P[ORC_RB_OBS];
+      if (obs != 0 || cut == 2) return m;
+      for (int i = 0; i < n; ++i)
+        if (!(x[4 * i] * x[4 * i + 1] > 0.0)) return m;
+      double p[4 * (ORC_MAXDIM / 4)], pt[ORC_MAXDIM], eta[ORC_MAXDIM], phi[ORC_MAXDIM];
+      if (orc_rambo(n, P[ORC_RB_SQRTS], x, p)) return NAN;
+      for (int i = 0; i < n; ++i) {
+        const double* pi = p + 4 * i;
+        double pabs = sqrt(pi[1] * pi[1] + pi[2] * pi[2] + pi[3] * pi[3]);
+        pt[i] = sqrt(pi[1] * pi[1] + pi[2] * pi[2]);
+        eta[i] = atanh(pi[3] / pabs);
+        phi[i] = atan2(pi[2], pi[1]);
+        if (cut == 0) m = fmin(m, rel_gap(pt[i], P[ORC_RB_PTMIN]));
+      }
+      for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+          double de = eta[i] - eta[j], dp = phi[i] - phi[j];
+          while (dp > M_PI) dp -= 2.0 * M_PI;
+          while (dp < -M_PI) dp += 2.0 * M_PI;
+          m = fmin(m, rel_gap(sqrt(de * de + dp * dp), P[ORC_RB_DRMIN]));
+        }
+      return m;
+    }
+    default:
+      return m;
+  }
+}
+
+int orc_cut_margin(const orc_fn* fn, int64_t n, const double* x, double* m) {
+  if (!fn_valid(fn)) return -1;
+  for (int64_t i = 0; i < n; ++i) m[i] = margin_point(fn, x + i * fn->ndim);
   return 0;
 }
 

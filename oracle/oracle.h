@@ -160,6 +160,15 @@ int orc_integrand_grad(const orc_fn* fn, int64_t n, const double* x,
                        double* grad);
 int orc_ntheta(const orc_fn* fn);
 
+/* Cut margins (test infrastructure): m[i] = the smallest relative distance
+ * |q - e| / |e| from its edge e of any quantity q that the integrand at
+ * x[i] compares with a cut or a discontinuity (RAMBO: each pT against the
+ * hard cut, each Delta R against its cut; discontinuous Genz: x_1, x_2
+ * against u_1, u_2; W: pT, |eta|, x1, x2 and the helicity-cell edge of
+ * 16 y5); INFINITY where it compares none.  A point with a small margin
+ * may fall on either side of its edge under rounding. */
+int orc_cut_margin(const orc_fn* fn, int64_t n, const double* x, double* m);
+
 /* RAMBO: n massless momenta (E, px, py, pz) from 4n numbers in (0, 1]. */
 int orc_rambo(int n, double sqrt_s, const double* rho, double* p);
 /* The RAMBO_BW integrand without the phase-space weight, from momenta. */
