@@ -238,10 +238,18 @@ struct DoubleGaussian {
 //   returns  cut * [mu_g / ((s12 - mu)^2 + mu_g^2)] * prod_i 1/s_{i,i+1}
 // (s_ij in units of s, mu = M^2/s, mu_g = M Gamma / s); the host multiplies
 // every sum by the constant V_n s^-3 (or the observable's own scale).
-// Invariants are formed as s_ij = pT_i pT_j (4 sinh^2(deta/2) + |u_i - u_j|^2),
-// u the unit transverse direction (|u_i - u_j| = 2 sin(dphi/2)), which has no
-// cancellation for nearly collinear pairs in FP32 and needs no atan2.  The
-// FP32 kernels use the quick forms of common.cuh; FP64 the library.
+// The invariants come from the isotropic momenta q_i of RAMBO's first step,
+// before its boost: with n_i the unit direction of q_i, 2 q_i.q_j =
+// q0_i q0_j |n_i - n_j|^2, the total mass is M^2 = sum_{i<j} 2 q_i.q_j, and
+// the boost and scaling that follow leave s_ij / s = 2 q_i.q_j / M^2.  Every
+// term is non-negative, so nothing cancels however strongly the system of
+// q's is boosted (forming M^2 = Q0^2 - |Q|^2 or s_ij from the boosted momenta
+// loses about gamma^2 of the precision, which in FP32 biased the estimate;
+// the Breit-Wigner amplifies an error of s12 by up to M / Gamma).  For two
+// partons s12 = s exactly.  The boosted momenta give pT, eta and the
+// transverse direction u for the cuts (|u_i - u_j| = 2 sin(dphi/2), no
+// atan2).
+// The FP32 kernels use the quick forms of common.cuh; FP64 the library.
 enum {
   RB_N = kScalar, RB_MU, RB_MUG, RB_MUG2, RB_PTMIN, RB_DR2, RB_CUT, RB_T,
   RB_INVWC, RB_OBS,
@@ -251,33 +259,19 @@ enum {
   RB_INVWC_GEV  // 1 / w_c                        (per GeV)
 };
 
-// sinh: FP32 through an odd Taylor polynomial below |x| = 1/2 (relative
-// error under 1e-8; exp(x) - exp(-x) would cancel there) and the quick
-// exponential above; FP64 through the library exponential.
-__device__ __forceinline__ float qsinh(float x) {
-  const float x2 = x * x;
-  const float poly = x * fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 5040.0f, 1.0f / 120.0f), 1.0f / 6.0f), 1.0f);
-  const float e = __expf(x);
-  const float big = 0.5f * (e - __fdividef(1.0f, e));
-  return fabsf(x) < 0.5f ? poly : big;
-}
-__device__ __forceinline__ double qsinh(double x) {
-  const double e = exp(x);
-  return 0.5 * (e - 1.0 / e);
-}
-
 template <typename T, int DM>
 struct RamboBW {
   static constexpr int NM = DM / 4;
 
   struct Event {
     T pt[NM], eta[NM], ux[NM], uy[NM];
+    T s[NM];  // s_{i, i+1 mod n} / s
   };
 
-  // Momenta -> (pT, eta, transverse direction).  Returns false for a
-  // zero-weight point.
+  // Momenta -> (pT, eta, transverse direction) and the cyclic invariants.
+  // Returns false for a zero-weight point.
   static __device__ __forceinline__ bool kinematics(const T (&x)[DM], int n, Event& ev) {
-    T E[NM], px[NM], py[NM], pz[NM];
+    T E[NM], nx[NM], ny[NM], nz[NM];
     T Q0 = T(0), Qx = T(0), Qy = T(0), Qz = T(0);
 #pragma unroll
     for (int i = 0; i < NM; ++i)
@@ -285,20 +279,36 @@ struct RamboBW {
         const T r1 = x[4 * i], r2 = x[4 * i + 1], r3 = x[4 * i + 2], r4 = x[4 * i + 3];
         if (!(r1 > T(0) && r2 > T(0))) return false;
         const T q0 = -(qlog_rel(r1) + qlog_rel(r2));
-        const T c = T(2) * r3 - T(1);
         const T sn = T(2) * qsqrt(r3 * (T(1) - r3));
         T sp, cp;
         qsincos2pi(r4, &sp, &cp);
         E[i] = q0;
-        px[i] = q0 * sn * cp;
-        py[i] = q0 * sn * sp;
-        pz[i] = q0 * c;
-        Q0 += E[i];
-        Qx += px[i];
-        Qy += py[i];
-        Qz += pz[i];
+        nx[i] = sn * cp;
+        ny[i] = sn * sp;
+        nz[i] = T(2) * r3 - T(1);
+        Q0 += q0;
+        Qx = vfma(q0, nx[i], Qx);
+        Qy = vfma(q0, ny[i], Qy);
+        Qz = vfma(q0, nz[i], Qz);
       }
-    const T MQ = qsqrt((Q0 - Qz) * (Q0 + Qz) - Qx * Qx - Qy * Qy);
+    // pair masses m_ij = 2 q_i.q_j, their sum M^2 and the cyclic ones
+    T M2 = T(0), cyc[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+#pragma unroll
+      for (int j = i + 1; j < NM; ++j)
+        if (j < n) {
+          const T dx = nx[i] - nx[j], dy = ny[i] - ny[j], dz = nz[i] - nz[j];
+          const T m = E[i] * E[j] * vfma(dx, dx, vfma(dy, dy, dz * dz));
+          M2 += m;
+          if (j == i + 1) cyc[i] = m;
+          if (i == 0 && j == n - 1) cyc[j] = m;  // (n-1, 0); for n = 2 the same pair twice
+        }
+    const T iM2 = qdiv(T(1), M2);
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      if (i < n) ev.s[i] = cyc[i] * iM2;
+    const T MQ = qsqrt(M2);
     const T iM = qdiv(T(1), MQ);
     const T bx = -Qx * iM, by = -Qy * iM, bz = -Qz * iM;
     const T gam = Q0 * iM;
@@ -306,11 +316,12 @@ struct RamboBW {
 #pragma unroll
     for (int i = 0; i < NM; ++i)
       if (i < n) {
-        const T bq = bx * px[i] + by * py[i] + bz * pz[i];
+        const T px = E[i] * nx[i], py = E[i] * ny[i], pz = E[i] * nz[i];
+        const T bq = bx * px + by * py + bz * pz;
         const T ab = A * bq + E[i];
-        const T qx = iM * vfma(ab, bx, px[i]);
-        const T qy = iM * vfma(ab, by, py[i]);
-        const T qz = iM * vfma(ab, bz, pz[i]);
+        const T qx = iM * vfma(ab, bx, px);
+        const T qy = iM * vfma(ab, by, py);
+        const T qz = iM * vfma(ab, bz, pz);
         const T pt2 = qx * qx + qy * qy;
         const T pt = qsqrt(pt2);
         const T pa = qsqrt(vfma(qz, qz, pt2));
@@ -327,11 +338,6 @@ struct RamboBW {
   static __device__ __forceinline__ T chord2(const Event& ev, int i, int j) {
     const T dx = ev.ux[i] - ev.ux[j], dy = ev.uy[i] - ev.uy[j];
     return vfma(dx, dx, dy * dy);
-  }
-
-  static __device__ __forceinline__ T sij(const Event& ev, int i, int j) {
-    const T sh = qsinh(T(0.5) * (ev.eta[i] - ev.eta[j]));
-    return ev.pt[i] * ev.pt[j] * vfma(T(4) * sh, sh, chord2(ev, i, j));
   }
 
   static __device__ __forceinline__ T bw(T s12, const T* P) {
@@ -376,14 +382,14 @@ struct RamboBW {
         for (int j = i + 1; j < NM; ++j)
           if (j < n && !dr_pass(ev, i, j, P)) return T(0);
     }
-    const T s12 = sij(ev, 0, 1);
+    const T s12 = ev.s[0];
     if (obs == 2) return s12;
     const T b = bw(s12, P);
     if (obs == 3) return b;
     T den = s12;
 #pragma unroll
     for (int i = 1; i < NM; ++i)
-      if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
+      if (i < n) den *= ev.s[i];
     return qdiv(cw * b, den);
   }
 
@@ -421,11 +427,11 @@ struct RamboBW {
         for (int j = i + 1; j < NM; ++j)
           if (j < n && !dr_pass(ev, i, j, P)) return T(0);
     }
-    const T s12 = sij(ev, 0, 1);
+    const T s12 = ev.s[0];
     T den = s12;
 #pragma unroll
     for (int i = 1; i < NM; ++i)
-      if (i < n) den *= sij(ev, i, (i + 1 == n) ? 0 : i + 1);
+      if (i < n) den *= ev.s[i];
     const T t = s12 - P[RB_MU], mug = P[RB_MUG];
     const T D = vfma(t, t, P[RB_MUG2]);
     const T iD = qdiv(T(1), D);

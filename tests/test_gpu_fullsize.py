@@ -107,6 +107,38 @@ def test_rambo5_full_size(gv, orc):
     assert abs(I - sub["I"]) <= 5 * math.sqrt(sub["var"] + var)
 
 
+def test_rambo5_full_iteration_in_the_tuned_shape(gv, orc):
+    """rambo5 at full size (2^24 points, 20 dims) in the launch shape the
+    autotuner picks (the one bench.py times), on a refined grid: sampled
+    words and bins bit-exact, then the whole iteration against the oracle's
+    on the same points and grid: I within 1e-5 relative and 0.1 sigma,
+    per-bin sums S1 within 1e-5 of sum |w|, S2 within 1e-5 of sum w^2 plus
+    2 eps of the cell itself (eps = 1e-4, the FP32 bar on one weight: a few
+    points can carry most of a cell's sum of squares, and their FP32 error
+    passes into it undiluted)."""
+    w = wl.WORKLOADS["rambo5"]
+    d, N, n = w["ndim"], w["nbins"], w["ncall"]
+    with _ctx(gv, w) as ctx:
+        gv.vegas_iterate(ctx, 2, refine=True)
+        gv.vegas_autotune(ctx)
+        edges = gv.vegas_get_grid(ctx)
+        I, var = gv.vegas_eval(ctx, 2)
+        _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
+        s = np.unique(np.concatenate([[0, n - 1], np.random.default_rng(12).integers(0, n, 4000)]))
+        dump = gv.vegas_sample_dump(ctx, 2, s)
+    cfg = orc.make_cfg(d, nbins=N, ncall=n, ybits=w["ybits"], seed=w["seed"])
+    fn = orc.Integrand(w["kind"], d, w["params"])
+    p = orc.sample_batch(cfg, edges, 2, s)
+    assert np.array_equal(dump["words"], p["words"]) and np.array_equal(dump["bins"], p["bins"])
+    o = orc.iteration(cfg, fn, edges, 2)
+    sig = math.sqrt(o["var"])
+    assert abs(I - o["I"]) <= 1e-5 * abs(o["I"]), (I, o["I"])
+    assert abs(I - o["I"]) <= 0.1 * sig
+    tot1, tot2 = np.abs(o["S1"]).sum(axis=1, keepdims=True), o["S2"].sum(axis=1, keepdims=True)
+    assert np.all(np.abs(bins[0] - o["S1"]) <= 1e-5 * tot1)
+    assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-5 * tot2 + 2e-4 * o["S2"])
+
+
 def test_rambo4_adjoint_full_size(gv):
     w = wl.WORKLOADS["rambo4_adjoint"]
     params = np.asarray(w["params"], dtype=np.float64)

@@ -7,7 +7,16 @@ Bars (stated per result):
     order differs from the oracle's sequential Neumaier order); estimates and
     refined edges within 1e-12 / 1e-13 relative.
   * FP32 forms (same 24-bit samples as the oracle): estimates within 1e-5
-    relative AND within 0.1 sigma; per-bin sums within 1e-5 * sum|w|.
+    relative AND within 0.1 sigma; per-bin sums S1 within 1e-5 * sum|w|, S2
+    within 1e-5 * sum w^2 + 2e-4 * S2 of the cell (a cell's sum of squares
+    can rest on a few points, whose FP32 error, 1e-4 at most per weight,
+    passes into it undiluted).
+  * Points one by one: FP64 values within 1e-12 relative; FP32 values within
+    2e-4 relative (1e-6 of the largest weight absolute) of the oracle at the
+    GPU's own FP32 point.  A point may fall on the other side of a cut or
+    discontinuity only where the oracle's cut margin (the relative distance
+    of pT, Delta R, a coordinate or a W cut quantity from its edge) is below
+    1e-13 in FP64 or 1e-4 in FP32.
 """
 import math
 
@@ -65,19 +74,27 @@ def test_words_bins_points(gv, orc, name, kind, d, params, kw, precision, ybits)
             o = orc.sample_batch(cfg, orc.uniform_grid(d, 50), it, s)
             assert np.array_equal(g["words"], o["words"])
             assert np.array_equal(g["bins"], o["bins"])
-            fo = orc.integrand(fn, o["x"]) * o["jac"]
             fg = g["f"] * g["jac"]
             if precision == 0:
                 assert np.array_equal(g["jac"], o["jac"])
                 np.testing.assert_allclose(g["x"], o["x"], rtol=4.5e-16, atol=1e-300)
+                fo = orc.integrand(fn, o["x"]) * o["jac"]
                 ok = np.isclose(fg, fo, rtol=1e-12, atol=1e-300)
+                edge = 1e-13  # a few hundred ulp of a cut quantity
+                margin = orc.cut_margin(fn, o["x"])
             else:
                 np.testing.assert_allclose(g["x"], o["x"], rtol=0, atol=3e-7)
+                # the oracle at the GPU's own FP32 point (the FP32 rounding of
+                # x is a different input, not an error of the integrand)
+                xg = np.ascontiguousarray(g["x"])
+                fo = orc.integrand(fn, xg) * g["jac"]
                 ok = np.isclose(fg, fo, rtol=2e-4, atol=1e-300 + 1e-6 * np.max(np.abs(fo)))
-            # cut decisions (and the discontinuous family's edges) may flip for
-            # points within rounding of the edge
-            flips = kind in (wl.RAMBO_BW, wl.GENZ_DISCONTINUOUS, wl.W_MUNU)
-            assert np.mean(ok) >= (0.99 if flips else 1.0), np.flatnonzero(~ok)[:10]
+                edge = 1e-4  # FP32 rounding of pT, Delta R, eta through the boost
+                margin = orc.cut_margin(fn, xg)
+            # a point may land on the other side of a cut or discontinuity only
+            # when the oracle puts its cut quantity within rounding of the edge
+            bad = np.flatnonzero(~ok & ~(margin < edge))
+            assert bad.size == 0, (bad[:10], fg[bad[:5]], fo[bad[:5]], margin[bad[:5]])
 
 
 def _cond_close(a, b, scale, tol):
@@ -94,7 +111,7 @@ def test_fp64_iteration_sums(gv, orc, name, kind, d, params, kw):
     o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 3)
     p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 3, np.arange(ncall))
     absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
-    tol = 1e-12 if kind != wl.RAMBO_BW else 1e-9  # RAMBO: cut-edge flips allowed below
+    tol = 1e-12
     assert abs(I - o["I"]) <= tol * max(absw.mean(), 1e-300)
     assert abs(math.sqrt(var) - math.sqrt(o["var"])) <= 1e-9 * math.sqrt(o["var"]) + 1e-300
     assert _cond_close(bins[0], o["S1"], absw.sum(), tol)
@@ -118,7 +135,8 @@ def test_fp32_iteration_vs_oracle(gv, orc, name, kind, d, params, kw, precision)
     p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 2, np.arange(ncall))
     absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
     assert _cond_close(bins[0], o["S1"], absw.sum(), 1e-5)
-    assert _cond_close(bins[1], o["S2"], (absw ** 2).sum(), 1e-5)
+    # S2: also within twice the per-point FP32 bar (1e-4) of the cell itself
+    assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-5 * (absw ** 2).sum() + 2e-4 * np.abs(o["S2"]))
 
 
 def test_vegas_loop_fp64_gauss4(gv, orc):
@@ -392,5 +410,24 @@ def test_two_body_rambo_fp64_matches_the_oracle(gv, orc):
     assert abs(I - o["I"]) <= 1e-12 * abs(o["I"])
     assert np.array_equal(g["words"], ob["words"])
     fo = orc.integrand(fn, ob["x"]) * ob["jac"]
-    ok = np.isclose(g["f"] * g["jac"], fo, rtol=1e-9, atol=1e-300)
-    assert np.mean(ok) >= 0.999
+    # every point: the momenta come from a boost whose rounding grows with
+    # gamma^2 of the isotropic system, 1e-11 at worst over these samples
+    np.testing.assert_allclose(g["f"] * g["jac"], fo, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("cut", [0, 1])
+@pytest.mark.parametrize("precision", [2, 1])
+def test_two_body_rambo_fp32_matches_the_oracle(gv, orc, cut, precision):
+    """The two-body RAMBO integrand in the FP32 forms on 2^20 identical
+    points: the estimate within 1e-5 relative and 0.1 sigma of the oracle's,
+    whose integrand is pinned to the closed form f = V_2 cut BW(s) / s^2."""
+    p = wl.rambo_params(2, cut=cut)
+    ncall = 1 << 20
+    with gv.vegas_create(wl.RAMBO_BW, 8, p, ncall=ncall, precision=precision, ybits=24) as ctx:
+        I, var = gv.vegas_eval(ctx, 2)
+    cfg = orc.make_cfg(8, nbins=50, ncall=ncall, ybits=24)
+    o = orc.iteration(cfg, orc.Integrand(wl.RAMBO_BW, 8, p), orc.uniform_grid(8, 50), 2)
+    sig = math.sqrt(o["var"])
+    assert abs(I - o["I"]) <= 1e-5 * abs(o["I"]), (I, o["I"])
+    assert abs(I - o["I"]) <= 0.1 * sig
+    assert abs(math.sqrt(var) - sig) <= 1e-3 * sig
