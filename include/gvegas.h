@@ -186,6 +186,10 @@ typedef struct {
 vegas_status vegas_create(const vegas_config* config,
                           const vegas_integrand* integrand, vegas_ctx** out);
 
+/* End of a run (Sec. 2.1: step 6 ends the loop; the sample main program of
+ * Appendix A runs one integration and exits): waits for the context stream,
+ * then frees every device and pinned buffer and cached graph of the
+ * context.  NULL is ignored. */
 void vegas_destroy(vegas_ctx* ctx);
 
 /* Steps 2-6, n_iter times (Sec. 2.1, step 6): each iteration evaluates NCALL
@@ -223,8 +227,13 @@ vegas_status bases_integrate(vegas_ctx* ctx, int itmx1, double acc1,
  * reads them; their estimates, cube sums and maxima are complete. */
 vegas_status vegas_get_grid(vegas_ctx* ctx, double* edges, double* bin_sums);
 
-/* Replace the grid (resume / freeze).  Edges must start at 0, end at 1 and
- * increase strictly on every axis, else VEGAS_EINVAL. */
+/* Replace the grid (step 5's output, Sec. 2.1).  BASES keeps the grid of its
+ * optimisation phase for the integration phase and for SPRING (Sec. 2.1);
+ * this puts a saved grid back, which with vegas_set_iteration resumes a run
+ * exactly where vegas_get_grid / vegas_get_iteration left it.  edges is a
+ * host array [ndim][nbins+1]; every axis must start at 0, end at 1 and
+ * increase strictly, else VEGAS_EINVAL (the grid is then unchanged).
+ * Stream-ordered (the tables are rebuilt on the device). */
 vegas_status vegas_set_grid(vegas_ctx* ctx, const double* edges);
 
 /* The iteration history of the current window: hist[i] = (I_i, sigma_i^2),
@@ -269,7 +278,11 @@ vegas_status vegas_create_user(const vegas_config* config, const char* source,
  * vegas_create_user.  Errors as there. */
 vegas_status vegas_user_compile(const vegas_config* config, const char* source);
 
-/* Replace the integrand parameters (same count as at creation). */
+/* Replace the integrand parameters (step 3 of Sec. 2.1; the paper compiles
+ * its integrand's constants into the user's gVegasFunc.cu, Appendix A, so a
+ * change means a rebuild).  Here they are device data read at run time: the
+ * same count and layout as at creation (host array), checked as there
+ * (VEGAS_EINVAL, context unchanged); captured graphs stay valid. */
 vegas_status vegas_set_params(vegas_ctx* ctx, const double* params,
                               int nparams);
 
@@ -279,8 +292,11 @@ vegas_status vegas_set_params(vegas_ctx* ctx, const double* params,
  * random numbers. */
 vegas_status vegas_eval(vegas_ctx* ctx, uint32_t it, double* I, double* var);
 
-/* Gradient of that estimate with respect to integrand parameters theta on
- * the frozen grid with the random numbers of iteration `it`:
+/* No counterpart in the paper, which computes integrals only (Sec. 5.2):
+ * the derivative of the iteration estimate of Sec. 2.1 step 4 with respect
+ * to integrand parameters theta, for fits of a resonance mass, width or cut
+ * threshold by gradient.  On the frozen grid with the random numbers of
+ * iteration `it` (common random numbers):
  *   dI/dtheta = (1/NCALL) sum_s J_s df/dtheta(x_s).
  * theta = (M, Gamma, T) for VG_RAMBO_BW, (c1, c2, w) for
  * VG_DOUBLE_GAUSSIAN, (u[d], a[d]) for VG_GENZ_GAUSSIAN; VEGAS_EINVAL for
@@ -389,13 +405,24 @@ vegas_status vegas_profile_frozen_pass(vegas_ctx* ctx, int n_pass, double* ms);
  * ------------------------------------------------------------------------ */
 typedef struct vegas_batch vegas_batch;
 
+/* The paper runs one integration per program and sizes one kernel call per
+ * iteration (Sec. 5.3: NCALL points in one call, 256 threads per block);
+ * the batch extends that call over many independent integrations of
+ * different dimension and NCALL.  Copies the n configs and integrands
+ * (host arrays), allocates the batch's device buffers and sets uniform
+ * grids (step 1 of Sec. 2.1 per instance).  VEGAS_EINVAL for a rule above
+ * broken, VEGAS_ENOMEM, VEGAS_ECUDA; vegas_batch_last_error(NULL) says
+ * which. */
 vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_integrand* integrands,
                                 vegas_batch** out);
 void vegas_batch_destroy(vegas_batch* batch);
 
-/* n_iter iterations (0..64) of every instance, refining after each when
- * refine != 0; out (nullable) receives one result per instance (combined
- * over the instance's window) and forces a synchronisation. */
+/* Steps 2-6 of Sec. 2.1 for every instance, n_iter times (0..64): one
+ * persistent sampling kernel and one finalisation kernel per iteration,
+ * the whole call one CUDA graph; refining after each iteration when
+ * refine != 0.  out (nullable, host array of n) receives one result per
+ * instance (combined over the instance's window) and forces a
+ * synchronisation.  No ACC stop (every instance runs n_iter). */
 vegas_status vegas_batch_iterate(vegas_batch* batch, int n_iter, int refine, vegas_result* out);
 
 /* Uniform grids, empty windows and iteration counters back to zero. */
@@ -452,9 +479,11 @@ vegas_status vegas_microbench(int op, double* rate);
  * as vegas_get_grid) followed by I, its variance, sum w, sum w^2 and the
  * count of non-finite weights.  Asynchronous: `out` is ready when the stream
  * reaches it.  Every intermediate lives in one static 8 MiB device array of
- * the library (held by every GPU that loads it until the process exits);
- * shapes whose partial sums do not fit in it (ndim nbins beyond about
- * 60 000 cells) are rejected with VEGAS_EINVAL.  The first call on a device
+ * the library (held by every GPU that loads it until the process exits).
+ * Every shape vegas_create accepts fits: the array holds the grid tables
+ * and one row of partial sums (16 ndim nbins + 40 bytes) per CTA, and where
+ * one row per resident CTA would not fit the pass runs fewer CTAs (about
+ * 60 at ndim nbins = 32 x 256), which is slower but not an error.  The first call on a device
  * looks up that array's device address, so make it before any stream
  * capture.  All calls share the array and each call overwrites it: calls
  * that overlap on the GPU (other streams, other host threads) race and give
@@ -462,8 +491,22 @@ vegas_status vegas_microbench(int op, double* rate);
 vegas_status vegas_eval_noalloc(const vegas_config* config, const vegas_integrand* integrand,
                                 const double* edges, uint32_t it, double* out);
 
-/* Message of the last failure on ctx (or of the calling thread when ctx is
- * NULL).  Never NULL. */
+/* Failure injection for tests (no counterpart in the paper).  Every device
+ * and pinned-host allocation the library makes goes through one wrapper.
+ * After vegas_fail_alloc_after(n) with n >= 0 the next n allocations
+ * succeed and the one after fails as an exhausted device would
+ * (cudaErrorMemoryAllocation, without calling the allocator); the hook then
+ * disarms itself.  n < 0 disarms it.  The failing call returns
+ * VEGAS_ENOMEM and frees what it had allocated.  Process-wide; any thread.
+ * vegas_alloc_count returns the number of allocations attempted so far
+ * (monotonic), so a test can count those a constructor makes. */
+void vegas_fail_alloc_after(int64_t n);
+uint64_t vegas_alloc_count(void);
+
+/* No counterpart in the paper (its programs print and stop).  Message of
+ * the last failure on ctx (or of the calling thread when ctx is NULL),
+ * owned by the library and valid until the next call on that context or
+ * thread.  Never NULL. */
 const char* vegas_last_error(const vegas_ctx* ctx);
 
 #endif /* __CUDACC_RTC__ */

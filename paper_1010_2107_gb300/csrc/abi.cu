@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -44,7 +45,42 @@ std::string vformat(const char* fmt, va_list ap) {
   return big;
 }
 
+// Allocation wrappers.  g_alloc_left: allocations still allowed before an
+// injected failure (-1: none armed); the failing call returns
+// cudaErrorMemoryAllocation without calling the allocator and disarms.
+std::atomic<long long> g_alloc_left{-1};
+std::atomic<unsigned long long> g_alloc_count{0};
+
+bool injected_failure() {
+  long long left = g_alloc_left.load();
+  while (left >= 0)
+    if (g_alloc_left.compare_exchange_weak(left, left - 1)) return left == 0;
+  return false;
+}
+
 }  // namespace
+
+extern "C" cudaError_t gv_dev_malloc(void** p, size_t bytes) {
+  g_alloc_count.fetch_add(1);
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+extern "C" cudaError_t gv_host_malloc(void** p, size_t bytes) {
+  g_alloc_count.fetch_add(1);
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+extern "C" void vegas_fail_alloc_after(int64_t n) { g_alloc_left.store(n < 0 ? -1 : (long long)n); }
+
+extern "C" uint64_t vegas_alloc_count(void) { return (uint64_t)g_alloc_count.load(); }
 
 struct vegas_ctx {
   vegas_config cfg{};
@@ -370,7 +406,7 @@ vegas_status configure_launch(vegas_ctx* c) {
     const size_t smem = c->ke.smem(d, N, cap);
     int o = 0;
     if (e != cudaSuccess || smem > 227 * 1024) return 0;
-    e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = gv_raise_smem_limit(c->ke.sample, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, c->ke.sample, c->threads, smem);
     return e == cudaSuccess ? o : 0;
   };
@@ -381,9 +417,9 @@ vegas_status configure_launch(vegas_ctx* c) {
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   if (t.occ < 1) return c->fail(VEGAS_EINVAL, "sampling kernel does not fit: %d threads, %d points per thread",
                                 c->threads, t.ppt);
-  // leave the attribute at the chosen size
+  // the limit covers the chosen size (it only grows: see gv_raise_smem_limit)
   c->smem = c->ke.smem(d, N, t.cap);
-  e = cudaFuncSetAttribute(c->ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem);
+  e = gv_raise_smem_limit(c->ke.sample, c->smem);
   if (e != cudaSuccess) return c->fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   c->cap = t.cap;
   c->ppt = t.ppt;
@@ -422,8 +458,8 @@ vegas_status configure_launch(vegas_ctx* c) {
     c->d_part_bins = nullptr;
     c->d_part_tot = nullptr;
     c->part_rows = 0;
-    CK(c, cudaMalloc(&c->d_part_bins, sizeof(double) * 2 * (size_t)d * N * rows));
-    CK(c, cudaMalloc(&c->d_part_tot, sizeof(double) * gv::kTotCols * (size_t)rows));
+    CK(c, gv_malloc(&c->d_part_bins, sizeof(double) * 2 * (size_t)d * N * rows));
+    CK(c, gv_malloc(&c->d_part_tot, sizeof(double) * gv::kTotCols * (size_t)rows));
     c->part_rows = rows;
   }
   destroy_graphs(c);
@@ -582,7 +618,7 @@ vegas_status stage(vegas_ctx* c, size_t n) {
   if (c->h_stage) cudaFreeHost(c->h_stage);
   c->h_stage = nullptr;
   c->h_stage_len = 0;
-  CK(c, cudaMallocHost(&c->h_stage, n * sizeof(double)));
+  CK(c, gv_malloc_host(&c->h_stage, n * sizeof(double)));
   c->h_stage_len = n;
   return VEGAS_OK;
 }
@@ -702,7 +738,7 @@ vegas_status finish_create(vegas_ctx* c, vegas_ctx** out) {
     c->own_stream = true;
   }
   auto alloc = [&](void** p, size_t bytes) -> vegas_status {
-    cudaError_t ae = cudaMalloc(p, bytes);
+    cudaError_t ae = gv_dev_malloc(p, bytes);
     if (ae != cudaSuccess)
       return c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(ae));
     return VEGAS_OK;
@@ -718,7 +754,7 @@ vegas_status finish_create(vegas_ctx* c, vegas_ctx** out) {
   if (!st) st = alloc((void**)&c->d_cube_max, sizeof(double) * G);
   if (!st) st = alloc((void**)&c->d_st, sizeof(GState));
   if (st) return bail(st);
-  if (cudaMallocHost(&c->h_st, sizeof(GState)) != cudaSuccess)
+  if (gv_malloc_host(&c->h_st, sizeof(GState)) != cudaSuccess)
     return bail(c->fail(VEGAS_ENOMEM, "cudaMallocHost(GState)"));
   memset(c->h_st, 0, sizeof(GState));
   c->h_st->acc = cfg->acc;
@@ -729,7 +765,7 @@ vegas_status finish_create(vegas_ctx* c, vegas_ctx** out) {
   if (c->ke.grad) {  // adjoint pass (vegas_grad): launch shape and partial rows
     c->grad_smem = c->ke.grad_smem(d, N);
     int occg = 0;
-    e = cudaFuncSetAttribute(c->ke.grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->grad_smem);
+    e = gv_raise_smem_limit(c->ke.grad, c->grad_smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occg, c->ke.grad, 256, c->grad_smem);
     if (e != cudaSuccess) return bail(c->fail(VEGAS_ECUDA, "adjoint launch: %s", cudaGetErrorString(e)));
     const int64_t want = (cfg->ncall + 255) / 256;
@@ -1004,7 +1040,7 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   auto grow = [&](void** p, size_t bytes) -> vegas_status {
     cudaFree(*p);
     *p = nullptr;
-    if (cudaMalloc(p, bytes) != cudaSuccess) return c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", bytes);
+    if (gv_dev_malloc(p, bytes) != cudaSuccess) return c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", bytes);
     return VEGAS_OK;
   };
   vegas_status st = VEGAS_OK;
@@ -1071,7 +1107,7 @@ vegas_status spring_generate(vegas_ctx* c, uint64_t trial0, uint32_t n_trials, d
   const size_t smem = (size_t)d * N * (f64 ? sizeof(double2) : sizeof(float2)) +
                       gv::kNumDerived * (f64 ? sizeof(double) : sizeof(float));
   int occ = 0;
-  CK(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CK(c, gv_raise_smem_limit(fn, smem));
   CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem));
   if (occ < 1) return c->fail(VEGAS_EINVAL, "SPRING kernel does not fit");
   const uint32_t blocks = std::min<uint32_t>(nchunks, (uint32_t)(c->sm_count * occ));
@@ -1195,7 +1231,7 @@ vegas_status vegas_sample_dump(vegas_ctx* c, uint32_t it, const uint64_t* s, int
   double *dx = nullptr, *dj = nullptr, *df = nullptr;
   vegas_status st = VEGAS_OK;
   auto A = [&](void** p, size_t b) {
-    if (!st && cudaMalloc(p, b) != cudaSuccess) st = c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", b);
+    if (!st && gv_dev_malloc(p, b) != cudaSuccess) st = c->fail(VEGAS_ENOMEM, "cudaMalloc(%zu)", b);
   };
   A((void**)&ds, n * sizeof(uint64_t));
   if (words) A((void**)&dw, n * W * sizeof(uint32_t));
@@ -1574,7 +1610,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
     const size_t sm = ke.smem(d, N, cap);
     int o = 0;
     if (e != cudaSuccess || sm > 227 * 1024) return 0;
-    e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    e = gv_raise_smem_limit(ke.sample, sm);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ke.sample, threads, sm);
     return e == cudaSuccess ? o : 0;
   };
@@ -1585,7 +1621,7 @@ extern "C" vegas_status vegas_eval_noalloc(const vegas_config* cfg, const vegas_
   if (t.occ < 1) return thread_fail(VEGAS_EINVAL, "sampling kernel does not fit in shared memory");
   const int ppt = t.ppt, cap = t.cap, occ = t.occ;
   const size_t smem = ke.smem(d, N, cap);
-  e = cudaFuncSetAttribute(ke.sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = gv_raise_smem_limit(ke.sample, smem);
   if (e != cudaSuccess) return thread_fail(VEGAS_ECUDA, "launch configuration: %s", cudaGetErrorString(e));
   const int dN = d * N;
   const size_t off_st = 0;

@@ -495,7 +495,7 @@ vegas_status build_items(vegas_batch* b) {
     cudaFree(b->d_rows);
     b->d_rows = nullptr;
     b->rows_cap = 0;
-    BK(b, cudaMalloc(&b->d_rows, row * esz));
+    BK(b, gv_dev_malloc(&b->d_rows, row * esz));
     b->rows_cap = row;
   }
   b->row_entries = row;
@@ -503,7 +503,7 @@ vegas_status build_items(vegas_batch* b) {
     cudaFree(b->d_items);
     b->d_items = nullptr;
     b->items_cap = 0;
-    BK(b, cudaMalloc(&b->d_items, b->items.size() * sizeof(BatchItem)));
+    BK(b, gv_malloc(&b->d_items, b->items.size() * sizeof(BatchItem)));
     b->items_cap = b->items.size();
   }
   BK(b, cudaMemcpyAsync(b->d_items, b->items.data(), b->items.size() * sizeof(BatchItem),
@@ -524,7 +524,7 @@ vegas_status configure(vegas_batch* b) {
     const size_t smem = batch_smem(b->prec, b->N, cap);
     int o = 0;
     if (e != cudaSuccess || smem > 227 * 1024) return 0;
-    e = cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = gv_raise_smem_limit(b->kernel, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, b->kernel, b->threads, smem);
     return e == cudaSuccess ? o : 0;
   };
@@ -534,7 +534,7 @@ vegas_status configure(vegas_batch* b) {
   BK(b, e);
   if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
   b->smem = batch_smem(b->prec, b->N, t.cap);
-  BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  BK(b, gv_raise_smem_limit(b->kernel, b->smem));
   b->cap = t.cap;
   b->ppt = t.ppt;
   b->occ = t.occ;
@@ -715,7 +715,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
     b->own_stream = true;
   }
   auto alloc = [&](void** p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) == cudaSuccess) return true;
+    if (gv_dev_malloc(p, bytes) == cudaSuccess) return true;
     b->fail(VEGAS_ENOMEM, "cudaMalloc(%zu) failed", bytes);
     return false;
   };
@@ -725,7 +725,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
       !alloc((void**)&b->d_tab32, sizeof(float2) * cells) || !alloc((void**)&b->d_st, sizeof(BatchState) * n) ||
       !alloc((void**)&b->d_head, sizeof(int)))
     return bail(VEGAS_ENOMEM);
-  if (cudaMallocHost(&b->h_st, sizeof(BatchState) * n) != cudaSuccess) {
+  if (gv_malloc_host(&b->h_st, sizeof(BatchState) * n) != cudaSuccess) {
     b->fail(VEGAS_ENOMEM, "cudaMallocHost failed");
     return bail(VEGAS_ENOMEM);
   }

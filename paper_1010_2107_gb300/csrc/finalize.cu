@@ -8,6 +8,10 @@
 //               alpha, rebinning to equal weight) and the last block of the
 //               totals the iteration estimate, the inverse-variance
 //               combination, chi^2 and the ACC test.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "refine.cuh"
@@ -250,6 +254,25 @@ cudaError_t gv_prepare_aux_kernels(void) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Dynamic shared-memory limit of a kernel on the current device, raised to
+// at least `bytes` and never lowered.  Contexts, batches and the
+// no-allocation pass share compiled kernels with different tile shapes;
+// captured graphs and later launches of each keep needing the size it
+// asked for, so the limit only grows (mutex: any host thread may call).
+cudaError_t gv_raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[std::make_pair(dev, fn)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s) {

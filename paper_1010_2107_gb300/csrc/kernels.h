@@ -187,6 +187,13 @@ struct DumpArgs {
 #ifndef __CUDACC_RTC__
 extern "C" {
 cudaError_t gv_prepare_aux_kernels(void);
+// Raise (never lower) a kernel's dynamic shared-memory limit to `bytes`.
+cudaError_t gv_raise_smem_limit(const void* fn, size_t bytes);
+// Every device (gv_dev_malloc) and pinned host (gv_host_malloc) allocation
+// of the library: cudaMalloc / cudaMallocHost behind a counter and the
+// failure injection of vegas_fail_alloc_after.
+cudaError_t gv_dev_malloc(void** p, size_t bytes);
+cudaError_t gv_host_malloc(void** p, size_t bytes);
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);
 cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
@@ -195,3 +202,14 @@ cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, fl
                              cudaStream_t s);
 }
 #endif  // __CUDACC_RTC__
+
+#ifndef __CUDACC_RTC__
+template <class T>
+inline cudaError_t gv_malloc(T** p, size_t bytes) {
+  return gv_dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t gv_malloc_host(T** p, size_t bytes) {
+  return gv_host_malloc(reinterpret_cast<void**>(p), bytes);
+}
+#endif

@@ -104,6 +104,8 @@ _SIGS = {
     "vegas_eval_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
                                           ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "vegas_last_error": (ctypes.c_char_p, [_P]),
+    "vegas_fail_alloc_after": (None, [ctypes.c_int64]),
+    "vegas_alloc_count": (ctypes.c_uint64, []),
     "vegas_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Config), ctypes.POINTER(IntegrandDesc),
                                           ctypes.POINTER(_P)]),
     "vegas_batch_destroy": (None, [_P]),
@@ -553,6 +555,17 @@ def vegas_batch_profile(b: Batch, n_pass: int = 5):
 def vegas_batch_last_error(b: Batch | None = None) -> str:
     m = lib().vegas_batch_last_error(b.handle if b else None)
     return m.decode() if m else ""
+
+
+def vegas_fail_alloc_after(n: int) -> None:
+    """Let the next n device / pinned allocations succeed and fail the one
+    after (n < 0: disarm); see include/gvegas.h."""
+    lib().vegas_fail_alloc_after(int(n))
+
+
+def vegas_alloc_count() -> int:
+    """Allocations the library has attempted so far (monotonic)."""
+    return int(lib().vegas_alloc_count())
 
 
 def vegas_last_error(ctx: Context | None = None) -> str:

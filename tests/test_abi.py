@@ -127,3 +127,13 @@ def test_user_kind_needs_its_own_constructor(gvlib):
         gv.vegas_create_user("template <typename T> __device__ T vegas_user_f(const T* x, int d, const T* p)"
                              " { return x[0]; }", 4, np.ones(gv.MAXUSERPARAMS + 1))
     assert e.value.status == gv.EINVAL
+
+
+def test_allocation_hook_is_host_only(gvlib):
+    """vegas_fail_alloc_after / vegas_alloc_count run without a device: the
+    counter is monotonic and arming or disarming it calls nothing on a GPU."""
+    gv = gvlib
+    c0 = gv.vegas_alloc_count()
+    gv.vegas_fail_alloc_after(3)
+    gv.vegas_fail_alloc_after(-1)
+    assert gv.vegas_alloc_count() >= c0 >= 0
