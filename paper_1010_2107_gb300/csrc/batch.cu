@@ -372,6 +372,8 @@ __global__ void k_batch_reset(BatchState* st, const BatchInst* inst, int n, int 
 
 }  // namespace gv
 
+#include "batch_class.cuh"
+
 using gv::BatchArgs;
 using gv::BatchInst;
 using gv::BatchItem;
@@ -393,7 +395,16 @@ struct vegas_batch {
   int sm_count = 0;
   // launch shape
   int threads = 256, rounds = 32, ctas = 0, cap = 16, ppt = 1, occ = 0;
+  int ppt_req = 0;         // points per thread per tile asked for (0: automatic)
   bool small_cap = false;  // tile capacity policy (gv::choose_tile)
+  // FP32 form with 24-bit words: one kernel per dimension class (d <= 4,
+  // <= 8, <= 16), each with its item range, tile and launch shape
+  bool by_class = false;
+  struct Class {
+    int first = 0, count = 0, cap = 4, ctas = 0, occ = 0;
+    size_t smem = 0;
+    const void* fn = nullptr;
+  } cls[3];
   size_t smem = 0;
   const void* kernel = nullptr;
   // host copies of the tables
@@ -464,18 +475,30 @@ size_t batch_smem(int prec, int N, int cap) {
   return prec == VG_FP64 ? gv::BatchSmem<double, 0>::total(N, cap) : gv::BatchSmem<float, 2>::total(N, cap);
 }
 
+// Dimension class of an instance for the per-class kernels: d <= 4, <= 8, <= 16.
+int dim_class(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : 2); }
+constexpr int kClassDim[3] = {4, 8, 16};
+
 // Items of `threads * rounds` points, instances in decreasing NCALL order so
-// that the small items come last; rows laid out in item order.
+// that the small items come last (grouped by dimension class first when the
+// per-class kernels run); rows laid out in item order.
 vegas_status build_items(vegas_batch* b) {
   const uint64_t tile = (uint64_t)b->threads * b->rounds;
   std::vector<int> order(b->n);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return b->cfg[x].ncall > b->cfg[y].ncall; });
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (b->by_class && dim_class(b->d[x]) != dim_class(b->d[y])) return dim_class(b->d[x]) > dim_class(b->d[y]);
+    return b->cfg[x].ncall > b->cfg[y].ncall;
+  });
   b->items.clear();
+  for (auto& c : b->cls) c.first = c.count = 0;
   size_t row = 0;
   for (int i : order) {
     BatchInst& I = b->inst[i];
+    if (b->by_class) {
+      auto& c = b->cls[dim_class(I.d)];
+      if (c.count == 0) c.first = (int)b->items.size();
+    }
     I.first_item = (int)b->items.size();
     const uint64_t n = (uint64_t)b->cfg[i].ncall;
     for (uint64_t s0 = 0; s0 < n; s0 += tile) {
@@ -488,7 +511,9 @@ vegas_status build_items(vegas_batch* b) {
       b->items.push_back(it);
     }
     I.nitems = (int)b->items.size() - I.first_item;
+    if (b->by_class) b->cls[dim_class(I.d)].count += I.nitems;
   }
+  for (auto& c : b->cls) c.ctas = std::min(c.count, b->sm_count * std::max(c.occ, 1));
   if (row > 0xFFFFFFFFull) return b->fail(VEGAS_EINVAL, "batch too large for the partial-row index");
   const size_t esz = b->prec == VG_FP64 ? sizeof(double) : sizeof(float2);
   if (row > b->rows_cap) {
@@ -515,7 +540,49 @@ vegas_status build_items(vegas_batch* b) {
   return VEGAS_OK;
 }
 
+template <int DMC>
+const void* class_kernel(int pif) {
+  return pif == 1 ? (const void*)&gv::k_batch_class<DMC, 1> : (const void*)&gv::k_batch_class<DMC, 2>;
+}
+
+// Per-class kernels: for each class its kernel (points in flight = the
+// tile's points per thread), bucket capacity and CTAs per SM.
+vegas_status configure_classes(vegas_batch* b) {
+  const int pif = b->ppt_req == 1 ? 1 : 2;
+  b->ppt = pif;
+  for (int k = 0; k < 3; ++k) {
+    auto& c = b->cls[k];
+    const int dmc = kClassDim[k], cells = dmc * b->N;
+    c.fn = k == 0 ? class_kernel<4>(pif) : (k == 1 ? class_kernel<8>(pif) : class_kernel<16>(pif));
+    BK(b, cudaFuncSetAttribute(c.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
+    cudaError_t e = cudaSuccess;
+    auto occ_of = [&](int cap, int) -> int {
+      const size_t smem = gv::ClassSmem::bytes(cells, dmc, cap);
+      int o = 0;
+      if (e != cudaSuccess || smem > 227 * 1024) return 0;
+      e = gv_raise_smem_limit(c.fn, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, c.fn, b->threads, smem);
+      return e == cudaSuccess ? o : 0;
+    };
+    int occ_cap = 0;
+    BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c.fn, b->threads, 0));
+    const gv::TileShape t = gv::choose_tile(b->threads, b->N, pif, pif, occ_cap, occ_of, b->small_cap);
+    BK(b, e);
+    if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel for %d axes does not fit: %d threads", dmc, b->threads);
+    c.cap = t.cap;
+    c.occ = t.occ;
+    c.smem = gv::ClassSmem::bytes(cells, dmc, t.cap);
+    BK(b, gv_raise_smem_limit(c.fn, c.smem));
+  }
+  b->cap = b->cls[2].cap;
+  b->occ = b->cls[2].occ;
+  b->ctas = b->sm_count * b->occ;
+  return build_items(b);
+}
+
 vegas_status configure(vegas_batch* b) {
+  if (b->by_class) return configure_classes(b);
   b->kernel = pick_batch_kernel(b->prec, b->ybits);
   BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared));
@@ -530,7 +597,7 @@ vegas_status configure(vegas_batch* b) {
   };
   int occ_cap = 0;
   BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, b->kernel, b->threads, 0));
-  const gv::TileShape t = gv::choose_tile(b->threads, b->N, 0, 1, occ_cap, occ_of, b->small_cap);
+  const gv::TileShape t = gv::choose_tile(b->threads, b->N, b->ppt_req, 1, occ_cap, occ_of, b->small_cap);
   BK(b, e);
   if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
   b->smem = batch_smem(b->prec, b->N, t.cap);
@@ -573,7 +640,17 @@ BatchArgs batch_args(const vegas_batch* b, int refine, int record) {
 }
 
 vegas_status launch_sample(vegas_batch* b, BatchArgs& A) {
-  BK(b, cudaMemsetAsync(b->d_head, 0, sizeof(int), b->stream));
+  BK(b, cudaMemsetAsync(b->d_head, 0, 4 * sizeof(int), b->stream));
+  if (b->by_class) {
+    for (int k = 2; k >= 0; --k) {  // the widest class first: the longest items
+      const auto& c = b->cls[k];
+      if (c.count == 0) continue;
+      gv::BatchRange R{c.first, c.count, b->d_head + 1 + k, c.cap};
+      void* args[] = {&A, &R};
+      BK(b, cudaLaunchKernel(c.fn, dim3(c.ctas), dim3(b->threads), args, c.smem, b->stream));
+    }
+    return VEGAS_OK;
+  }
   void* args[] = {&A};
   BK(b, cudaLaunchKernel(b->kernel, dim3(b->ctas), dim3(b->threads), args, b->smem, b->stream));
   return VEGAS_OK;
@@ -658,6 +735,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
   b->prec = prec;
   b->ybits = ybits;
   b->seed = c0.seed;
+  b->by_class = prec == VG_FP32_ACCCOMP && ybits == 24;
   b->cfg.assign(cfgs, cfgs + n);
   b->derived.assign((size_t)n * gv::kNumDerived, 0.0);
   b->inst.resize(n);
@@ -723,7 +801,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
       !alloc((void**)&b->d_edges, sizeof(double) * edges) || !alloc((void**)&b->d_derived, sizeof(double) * b->derived.size()) ||
       !alloc((void**)&b->d_bins, sizeof(double) * 2 * cells) || !alloc((void**)&b->d_tab64, sizeof(double2) * cells) ||
       !alloc((void**)&b->d_tab32, sizeof(float2) * cells) || !alloc((void**)&b->d_st, sizeof(BatchState) * n) ||
-      !alloc((void**)&b->d_head, sizeof(int)))
+      !alloc((void**)&b->d_head, 4 * sizeof(int)))
     return bail(VEGAS_ENOMEM);
   if (gv_malloc_host(&b->h_st, sizeof(BatchState) * n) != cudaSuccess) {
     b->fail(VEGAS_ENOMEM, "cudaMallocHost failed");
@@ -845,6 +923,29 @@ vegas_status vegas_batch_set_launch(vegas_batch* b, int threads, int rounds) {
   return configure(b);
 }
 
+vegas_status vegas_batch_set_tile(vegas_batch* b, int points_per_thread) {
+  if (!b) return bfail("batch is NULL");
+  const int hi = b->by_class ? 2 : 4;
+  if (points_per_thread < 0 || points_per_thread > hi)
+    return b->fail(VEGAS_EINVAL, "points_per_thread must be in 0..%d (0: automatic)", hi);
+  BK(b, cudaStreamSynchronize(b->stream));
+  const int p0 = b->ppt_req;
+  b->ppt_req = points_per_thread;
+  vegas_status st = configure(b);
+  if (st) {
+    b->ppt_req = p0;
+    configure(b);
+  }
+  return st;
+}
+
+vegas_status vegas_batch_get_tile(vegas_batch* b, int* points_per_thread, int* cap) {
+  if (!b) return bfail("batch is NULL");
+  if (points_per_thread) *points_per_thread = b->ppt;
+  if (cap) *cap = b->cap;
+  return VEGAS_OK;
+}
+
 vegas_status vegas_batch_get_launch(vegas_batch* b, int* threads, int* rounds, int* ctas, int* items) {
   if (!b) return bfail("batch is NULL");
   if (threads) *threads = b->threads;
@@ -890,15 +991,16 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   static const int kThreads[] = {128, 256};
   static const int kRounds[] = {8, 16, 32, 64, 128};
   struct Cand {
-    int t, r;
+    int t, r, p;
     bool small;
     double ms;
   };
   std::vector<Cand> cands;
-  // one warm-up pass, then the mean of n passes, for shape (t, r) and
-  // capacity policy `small`
-  auto time_shape = [&](int t, int r, bool small, int n, double* out) -> vegas_status {
+  // one warm-up pass, then the mean of n passes, for shape (t, r), tile p
+  // (the per-class kernels: points in flight) and capacity policy `small`
+  auto time_shape = [&](int t, int r, int p, bool small, int n, double* out) -> vegas_status {
     b->small_cap = small;
+    b->ppt_req = p;
     vegas_status st = vegas_batch_set_launch(b, t, r);
     double m[2];
     if (!st) st = vegas_batch_profile(b, 1, m);
@@ -906,31 +1008,34 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
     if (!st) *out = m[0];
     return st;
   };
+  const std::vector<int> tiles = b->by_class ? std::vector<int>{1, 2} : std::vector<int>{0};
   for (int t : kThreads)
-    for (int r : kRounds) {
-      int cap_large = -1;  // a repeated tile is not timed twice
-      for (bool small : {false, true}) {
-        double m = 0.0;
-        vegas_status st = time_shape(t, r, small, 3, &m);
-        if (st) return st;
-        if (small && b->cap == cap_large) continue;
-        if (!small) cap_large = b->cap;
-        cands.push_back({t, r, small, m});
+    for (int r : kRounds)
+      for (int p : tiles) {
+        int cap_large = -1;  // a repeated tile is not timed twice
+        for (bool small : {false, true}) {
+          double m = 0.0;
+          vegas_status st = time_shape(t, r, p, small, 3, &m);
+          if (st) return st;
+          if (small && b->cap == cap_large) continue;
+          if (!small) cap_large = b->cap;
+          cands.push_back({t, r, p, small, m});
+        }
       }
-    }
   // the three fastest again in interleaved rounds, keeping each one's best
   std::sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
   cands.resize(std::min<size_t>(cands.size(), 3));
   for (int k = 0; k < 3; ++k)
     for (Cand& c : cands) {
       double m = 0.0;
-      vegas_status st = time_shape(c.t, c.r, c.small, 3, &m);
+      vegas_status st = time_shape(c.t, c.r, c.p, c.small, 3, &m);
       if (st) return st;
       c.ms = k == 0 ? m : std::min(c.ms, m);
     }
   const Cand best = *std::min_element(cands.begin(), cands.end(),
                                       [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
   b->small_cap = best.small;
+  b->ppt_req = best.p;
   vegas_status st = vegas_batch_set_launch(b, best.t, best.r);
   if (st) return st;
   if (threads) *threads = best.t;

@@ -117,6 +117,8 @@ _SIGS = {
     "vegas_batch_get_launch": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
+    "vegas_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vegas_batch_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_batch_profile": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_batch_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -538,6 +540,16 @@ def vegas_batch_get_launch(b: Batch):
     _bcheck(lib().vegas_batch_get_launch(b.handle, ctypes.byref(t), ctypes.byref(r), ctypes.byref(c),
                                          ctypes.byref(it)), b.handle)
     return dict(threads=t.value, rounds=r.value, ctas=c.value, items=it.value)
+
+
+def vegas_batch_set_tile(b: Batch, points_per_thread: int = 0):
+    _bcheck(lib().vegas_batch_set_tile(b.handle, int(points_per_thread)), b.handle)
+
+
+def vegas_batch_get_tile(b: Batch):
+    p, c = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().vegas_batch_get_tile(b.handle, ctypes.byref(p), ctypes.byref(c)), b.handle)
+    return dict(points_per_thread=p.value, cap=c.value)
 
 
 def vegas_batch_autotune(b: Batch):
