@@ -26,58 +26,12 @@
 #include <utility>
 #include <vector>
 
+#include "batch_types.cuh"
 #include "kernels.h"
 #include "refine.cuh"
 #include "sample_kernel.cuh"
 
 namespace gv {
-
-constexpr int kBatchHist = 64;   // iterations kept per instance
-constexpr int kBatchDM = 16;     // compile-time dimension bound
-constexpr int kRowTail = 3;      // sum w, sum w^2, non-finite count
-
-struct BatchInst {
-  int kind, d, first_item, nitems;
-  uint64_t ncall;
-  uint32_t instance;
-  int tab_off;    // cells: [d][N] in tab64 / tab32
-  int edge_off;   // [d][N+1] in edges
-  int bins_off;   // [2][d][N] in bins
-  double alpha;
-};
-
-struct BatchItem {
-  int inst;
-  uint32_t s0, count;
-  uint32_t row;   // offset of the item's partial row (2 d N + kRowTail entries)
-};
-
-struct BatchState {
-  uint32_t it;
-  int nhist;
-  long long nonfinite, samples;
-  double I, sigma, chi2, last_I, last_var;
-  double hist[kBatchHist][2];
-};
-
-struct BatchArgs {
-  int n, nitems, N, cap, ppt;
-  uint32_t key0, key1;
-  uint32_t ks[kPhiloxKeyWords];  // Philox round keys of (key0, key1)
-  const BatchInst* inst;
-  const BatchItem* items;
-  const void* tab;        // float2 (FP32 form) or double2 (FP64) cells
-  const double* dparams;  // [n][kNumDerived]
-  int* head;              // next item
-  void* rows;             // float2 pairs (FP32 form) or doubles
-  BatchState* st;
-  double* edges;
-  double2* tab64;
-  float2* tab32;
-  double* bins;
-  const int2* axis_map;   // finalisation block -> (instance, axis)
-  int naxes, refine, record, pair32;
-};
 
 // Integrand dispatch for the batch: the family is uniform over an item.
 // KIND >= 0 fixes it at compile time; -1 switches per point.
@@ -372,7 +326,7 @@ __global__ void k_batch_reset(BatchState* st, const BatchInst* inst, int n, int 
 
 }  // namespace gv
 
-#include "batch_class.cuh"
+#include "batch_dim.cuh"
 
 using gv::BatchArgs;
 using gv::BatchInst;
@@ -397,14 +351,18 @@ struct vegas_batch {
   int threads = 256, rounds = 32, ctas = 0, cap = 16, ppt = 1, occ = 0;
   int ppt_req = 0;         // points per thread per tile asked for (0: automatic)
   bool small_cap = false;  // tile capacity policy (gv::choose_tile)
-  // FP32 form with 24-bit words: one kernel per dimension class (d <= 4,
-  // <= 8, <= 16), each with its item range, tile and launch shape
-  bool by_class = false;
-  struct Class {
+  // FP32 form with 24-bit words: one kernel per exact dimension d = 1..16,
+  // each with its item range, tile and launch shape, run concurrently on
+  // the auxiliary streams (forked from and joined to `stream`)
+  bool by_dim = false;
+  struct Dim {
     int first = 0, count = 0, cap = 4, ctas = 0, occ = 0;
     size_t smem = 0;
     const void* fn = nullptr;
-  } cls[3];
+  } dims[gv::kBatchDM];
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t fork = nullptr, join[kAux] = {};
   size_t smem = 0;
   const void* kernel = nullptr;
   // host copies of the tables
@@ -475,28 +433,24 @@ size_t batch_smem(int prec, int N, int cap) {
   return prec == VG_FP64 ? gv::BatchSmem<double, 0>::total(N, cap) : gv::BatchSmem<float, 2>::total(N, cap);
 }
 
-// Dimension class of an instance for the per-class kernels: d <= 4, <= 8, <= 16.
-int dim_class(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : 2); }
-constexpr int kClassDim[3] = {4, 8, 16};
-
 // Items of `threads * rounds` points, instances in decreasing NCALL order so
-// that the small items come last (grouped by dimension class first when the
-// per-class kernels run); rows laid out in item order.
+// that the small items come last (grouped by dimension first, widest first,
+// when the dimension kernels run); rows laid out in item order.
 vegas_status build_items(vegas_batch* b) {
   const uint64_t tile = (uint64_t)b->threads * b->rounds;
   std::vector<int> order(b->n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    if (b->by_class && dim_class(b->d[x]) != dim_class(b->d[y])) return dim_class(b->d[x]) > dim_class(b->d[y]);
+    if (b->by_dim && b->d[x] != b->d[y]) return b->d[x] > b->d[y];
     return b->cfg[x].ncall > b->cfg[y].ncall;
   });
   b->items.clear();
-  for (auto& c : b->cls) c.first = c.count = 0;
+  for (auto& c : b->dims) c.first = c.count = 0;
   size_t row = 0;
   for (int i : order) {
     BatchInst& I = b->inst[i];
-    if (b->by_class) {
-      auto& c = b->cls[dim_class(I.d)];
+    if (b->by_dim) {
+      auto& c = b->dims[I.d - 1];
       if (c.count == 0) c.first = (int)b->items.size();
     }
     I.first_item = (int)b->items.size();
@@ -511,9 +465,9 @@ vegas_status build_items(vegas_batch* b) {
       b->items.push_back(it);
     }
     I.nitems = (int)b->items.size() - I.first_item;
-    if (b->by_class) b->cls[dim_class(I.d)].count += I.nitems;
+    if (b->by_dim) b->dims[I.d - 1].count += I.nitems;
   }
-  for (auto& c : b->cls) c.ctas = std::min(c.count, b->sm_count * std::max(c.occ, 1));
+  for (auto& c : b->dims) c.ctas = std::min(c.count, b->sm_count * std::max(c.occ, 1));
   if (row > 0xFFFFFFFFull) return b->fail(VEGAS_EINVAL, "batch too large for the partial-row index");
   const size_t esz = b->prec == VG_FP64 ? sizeof(double) : sizeof(float2);
   if (row > b->rows_cap) {
@@ -540,25 +494,26 @@ vegas_status build_items(vegas_batch* b) {
   return VEGAS_OK;
 }
 
-template <int DMC>
-const void* class_kernel(int pif) {
-  return pif == 1 ? (const void*)&gv::k_batch_class<DMC, 1> : (const void*)&gv::k_batch_class<DMC, 2>;
-}
-
-// Per-class kernels: for each class its kernel (points in flight = the
-// tile's points per thread), bucket capacity and CTAs per SM.
-vegas_status configure_classes(vegas_batch* b) {
+// Dimension kernels: for each dimension present its kernel (points in
+// flight = the tile's points per thread), bucket capacity and CTAs per SM.
+vegas_status configure_dims(vegas_batch* b) {
   const int pif = b->ppt_req == 1 ? 1 : 2;
   b->ppt = pif;
-  for (int k = 0; k < 3; ++k) {
-    auto& c = b->cls[k];
-    const int dmc = kClassDim[k], cells = dmc * b->N;
-    c.fn = k == 0 ? class_kernel<4>(pif) : (k == 1 ? class_kernel<8>(pif) : class_kernel<16>(pif));
+  bool present[gv::kBatchDM] = {};
+  for (int i = 0; i < b->n; ++i) present[b->d[i] - 1] = true;
+  int widest = 0;
+  for (int d = 1; d <= gv::kBatchDM; ++d) {
+    auto& c = b->dims[d - 1];
+    c.occ = 0;
+    if (!present[d - 1]) continue;
+    widest = d;
+    const int cells = d * b->N;
+    c.fn = d <= 8 ? gv_batch_dim_kernel_lo(d, pif) : gv_batch_dim_kernel_hi(d, pif);
     BK(b, cudaFuncSetAttribute(c.fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared));
     cudaError_t e = cudaSuccess;
     auto occ_of = [&](int cap, int) -> int {
-      const size_t smem = gv::ClassSmem::bytes(cells, dmc, cap);
+      const size_t smem = gv::DimSmem::bytes(cells, d, cap);
       int o = 0;
       if (e != cudaSuccess || smem > 227 * 1024) return 0;
       e = gv_raise_smem_limit(c.fn, smem);
@@ -569,20 +524,20 @@ vegas_status configure_classes(vegas_batch* b) {
     BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c.fn, b->threads, 0));
     const gv::TileShape t = gv::choose_tile(b->threads, b->N, pif, pif, occ_cap, occ_of, b->small_cap);
     BK(b, e);
-    if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel for %d axes does not fit: %d threads", dmc, b->threads);
-    c.cap = t.cap;
+    if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel for %d axes does not fit: %d threads", d, b->threads);
+    c.cap = gv::DimSmem::stride(t.cap);  // the row holds this many slots
     c.occ = t.occ;
-    c.smem = gv::ClassSmem::bytes(cells, dmc, t.cap);
+    c.smem = gv::DimSmem::bytes(cells, d, c.cap);
     BK(b, gv_raise_smem_limit(c.fn, c.smem));
   }
-  b->cap = b->cls[2].cap;
-  b->occ = b->cls[2].occ;
+  b->cap = widest ? b->dims[widest - 1].cap : 0;
+  b->occ = widest ? b->dims[widest - 1].occ : 0;
   b->ctas = b->sm_count * b->occ;
   return build_items(b);
 }
 
 vegas_status configure(vegas_batch* b) {
-  if (b->by_class) return configure_classes(b);
+  if (b->by_dim) return configure_dims(b);
   b->kernel = pick_batch_kernel(b->prec, b->ybits);
   BK(b, cudaFuncSetAttribute(b->kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared));
@@ -640,14 +595,25 @@ BatchArgs batch_args(const vegas_batch* b, int refine, int record) {
 }
 
 vegas_status launch_sample(vegas_batch* b, BatchArgs& A) {
-  BK(b, cudaMemsetAsync(b->d_head, 0, 4 * sizeof(int), b->stream));
-  if (b->by_class) {
-    for (int k = 2; k >= 0; --k) {  // the widest class first: the longest items
-      const auto& c = b->cls[k];
+  BK(b, cudaMemsetAsync(b->d_head, 0, (1 + gv::kBatchDM) * sizeof(int), b->stream));
+  if (b->by_dim) {
+    // fork: the dimension kernels on the auxiliary streams (the widest, with
+    // the longest items, first), then join them back
+    BK(b, cudaEventRecord(b->fork, b->stream));
+    int k = 0;
+    for (int d = gv::kBatchDM; d >= 1; --d) {
+      const auto& c = b->dims[d - 1];
       if (c.count == 0) continue;
-      gv::BatchRange R{c.first, c.count, b->d_head + 1 + k, c.cap};
+      cudaStream_t s = b->aux[k % vegas_batch::kAux];
+      if (k < vegas_batch::kAux) BK(b, cudaStreamWaitEvent(s, b->fork, 0));
+      gv::BatchRange R{c.first, c.count, b->d_head + d, c.cap};
       void* args[] = {&A, &R};
-      BK(b, cudaLaunchKernel(c.fn, dim3(c.ctas), dim3(b->threads), args, c.smem, b->stream));
+      BK(b, cudaLaunchKernel(c.fn, dim3(c.ctas), dim3(b->threads), args, c.smem, s));
+      ++k;
+    }
+    for (int i = 0; i < std::min(k, vegas_batch::kAux); ++i) {
+      BK(b, cudaEventRecord(b->join[i], b->aux[i]));
+      BK(b, cudaStreamWaitEvent(b->stream, b->join[i], 0));
     }
     return VEGAS_OK;
   }
@@ -694,6 +660,11 @@ void vegas_batch_destroy(vegas_batch* b) {
   cudaFree(b->d_st);
   cudaFree(b->d_head);
   if (b->h_st) cudaFreeHost(b->h_st);
+  for (int i = 0; i < vegas_batch::kAux; ++i) {
+    if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -735,7 +706,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
   b->prec = prec;
   b->ybits = ybits;
   b->seed = c0.seed;
-  b->by_class = prec == VG_FP32_ACCCOMP && ybits == 24;
+  b->by_dim = prec == VG_FP32_ACCCOMP && ybits == 24;
   b->cfg.assign(cfgs, cfgs + n);
   b->derived.assign((size_t)n * gv::kNumDerived, 0.0);
   b->inst.resize(n);
@@ -792,6 +763,17 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
     }
     b->own_stream = true;
   }
+  if (b->by_dim) {  // the streams and events of the dimension kernels' fork and join
+    e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < vegas_batch::kAux && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      b->fail(VEGAS_ECUDA, "streams: %s", cudaGetErrorString(e));
+      return bail(VEGAS_ECUDA);
+    }
+  }
   auto alloc = [&](void** p, size_t bytes) -> bool {
     if (gv_dev_malloc(p, bytes) == cudaSuccess) return true;
     b->fail(VEGAS_ENOMEM, "cudaMalloc(%zu) failed", bytes);
@@ -801,7 +783,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
       !alloc((void**)&b->d_edges, sizeof(double) * edges) || !alloc((void**)&b->d_derived, sizeof(double) * b->derived.size()) ||
       !alloc((void**)&b->d_bins, sizeof(double) * 2 * cells) || !alloc((void**)&b->d_tab64, sizeof(double2) * cells) ||
       !alloc((void**)&b->d_tab32, sizeof(float2) * cells) || !alloc((void**)&b->d_st, sizeof(BatchState) * n) ||
-      !alloc((void**)&b->d_head, 4 * sizeof(int)))
+      !alloc((void**)&b->d_head, (1 + gv::kBatchDM) * sizeof(int)))
     return bail(VEGAS_ENOMEM);
   if (gv_malloc_host(&b->h_st, sizeof(BatchState) * n) != cudaSuccess) {
     b->fail(VEGAS_ENOMEM, "cudaMallocHost failed");
@@ -925,7 +907,7 @@ vegas_status vegas_batch_set_launch(vegas_batch* b, int threads, int rounds) {
 
 vegas_status vegas_batch_set_tile(vegas_batch* b, int points_per_thread) {
   if (!b) return bfail("batch is NULL");
-  const int hi = b->by_class ? 2 : 4;
+  const int hi = b->by_dim ? 2 : 4;
   if (points_per_thread < 0 || points_per_thread > hi)
     return b->fail(VEGAS_EINVAL, "points_per_thread must be in 0..%d (0: automatic)", hi);
   BK(b, cudaStreamSynchronize(b->stream));
@@ -1008,7 +990,7 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
     if (!st) *out = m[0];
     return st;
   };
-  const std::vector<int> tiles = b->by_class ? std::vector<int>{1, 2} : std::vector<int>{0};
+  const std::vector<int> tiles = b->by_dim ? std::vector<int>{1, 2} : std::vector<int>{0};
   for (int t : kThreads)
     for (int r : kRounds)
       for (int p : tiles) {

@@ -194,6 +194,10 @@ cudaError_t gv_raise_smem_limit(const void* fn, size_t bytes);
 // failure injection of vegas_fail_alloc_after.
 cudaError_t gv_dev_malloc(void** p, size_t bytes);
 cudaError_t gv_host_malloc(void** p, size_t bytes);
+// The batched dimension kernels k_batch_dim<d, pif> (batch_dims_lo.cu:
+// d = 1..8, batch_dims_hi.cu: d = 9..16); null outside the range.
+const void* gv_batch_dim_kernel_lo(int d, int pif);
+const void* gv_batch_dim_kernel_hi(int d, int pif);
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);
 cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
