@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 VEGAS / BASES hot path.
 
-Default workload (``dgauss8``): BASES with hypercube stratification (4 divisions
-per axis: 65 536 cubes x 64 points), d = 8 two-peak Gaussian, FP32 map and
-integrand with compensated FP32 / FP64 sums, 50 bins per axis, 5 grid-optimising
-+ 5 frozen-grid iterations of NCALL = 2^22 points.  One step = the whole
-two-phase BASES run from the uniform grid (10 iterations, 41.9 M points).
+Default workload (``genz256``, the largest configuration): 256 independent
+Genz integrands (product peak, corner peak, oscillatory; d from 2 to 16;
+2^16..2^22 points each, about 2.5e8 points per iteration), FP32 map and
+integrand with compensated FP32 sums, 50 bins per axis, 8 refining VEGAS
+iterations of every instance from the uniform grid per step, as one batch.
 
 Metric: points (samples) per second through the iteration loop, whole job.
-Also reported: the plain FP64 GPU path on the same points (speed-up), the
-roofline of the sampling kernel, the reduction pass in GB/s, the CPU oracle
-timed on the host, and the end-to-end rate through the C ABI with host buffers.
+Also reported: the plain FP64 GPU path on the same points (speed-up, and the
+largest difference of the two estimates in units of sigma), the roofline of
+the sampling pass, the CPU oracle timed on the host, the end-to-end rate
+through the C ABI with host buffers, and (one GPU) the same figures for the
+dgauss8 BASES, rambo5 and rambo4_adjoint workloads under ``workloads``.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -242,28 +244,75 @@ def oracle_rate_allcores(name: str):
     return n / dt, n, dt, P
 
 
+def _genz_sample(budget=1 << 22, stride=1, start=0):
+    """Instances start, start + stride, ... of the batched workload, taken in
+    order until they hold about `budget` points."""
+    from paper_1010_2107_gb300 import workloads as wl
+    insts = wl.genz_batch(wl.GENZ256["count"], wl.GENZ256["seed"])
+    chosen, tot = [], 0
+    for ins in insts[start::stride]:
+        chosen.append(ins)
+        tot += ins["ncall"]
+        if tot >= budget:
+            break
+    return chosen, tot
+
+
+def _oracle_genz(insts):
+    """One iteration of each instance on its uniform grid through the oracle
+    as it stands; returns (points, seconds)."""
+    import oracle
+    from paper_1010_2107_gb300 import workloads as wl
+    t = time.perf_counter()
+    for ins in insts:
+        cfg = oracle.make_cfg(ins["ndim"], nbins=wl.GENZ256["nbins"], ncall=ins["ncall"], ybits=24,
+                              seed=wl.GENZ256["sample_seed"], instance=ins["instance"])
+        fn = oracle.Integrand(ins["kind"], ins["ndim"], ins["params"])
+        oracle.iteration(cfg, fn, oracle.uniform_grid(ins["ndim"], wl.GENZ256["nbins"]), 0)
+    return sum(i["ncall"] for i in insts), time.perf_counter() - t
+
+
+def oracle_rate_batched():
+    """The oracle, single-threaded, on the leading instances of the batch
+    (about 2^22 points): (points/s, points, seconds, instances)."""
+    import oracle
+    oracle.build()
+    chosen, _ = _genz_sample()
+    n, dt = _oracle_genz(chosen)
+    return n / dt, n, dt, len(chosen)
+
+
+def _oracle_genz_worker(job):
+    start, stride = job
+    import oracle
+    oracle.build()
+    chosen, _ = _genz_sample(1 << 21, stride, start)
+    return _oracle_genz(chosen)
+
+
+def oracle_rate_batched_allcores():
+    """One oracle process per core, each on its own instances of the batch
+    (every P-th, about 2^21 points): points of all over the slowest time."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    P = len(os.sched_getaffinity(0))
+    with ProcessPoolExecutor(max_workers=P, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_genz_worker, [(p, P) for p in range(P)], timeout=600))
+    n = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return n / dt, n, dt, P
+
+
 def _reference_step(name):
     """One step of the reference arm (the oracle as it stands): returns a
     callable giving (points, seconds, description of the sample)."""
     import oracle
     if name == "genz256":
-        from paper_1010_2107_gb300 import workloads as wl
-        insts = wl.genz_batch(wl.GENZ256["count"], wl.GENZ256["seed"])
-        chosen, tot = [], 0
-        for ins in insts:  # the leading instances, about 2^22 points in all
-            chosen.append(ins)
-            tot += ins["ncall"]
-            if tot >= 1 << 22:
-                break
+        chosen, tot = _genz_sample()  # the leading instances, about 2^22 points in all
 
         def step():
-            t = time.perf_counter()
-            for ins in chosen:
-                cfg = oracle.make_cfg(ins["ndim"], nbins=wl.GENZ256["nbins"], ncall=ins["ncall"], ybits=24,
-                                      seed=wl.GENZ256["sample_seed"], instance=ins["instance"])
-                fn = oracle.Integrand(ins["kind"], ins["ndim"], ins["params"])
-                oracle.iteration(cfg, fn, oracle.uniform_grid(ins["ndim"], wl.GENZ256["nbins"]), 0)
-            return tot, time.perf_counter() - t, f"one iteration of the first {len(chosen)} instances ({tot} points)"
+            n, dt = _oracle_genz(chosen)
+            return n, dt, f"one iteration of the first {len(chosen)} instances ({n} points)"
         return step
     w = _workload(name)
     if w.get("mode") == "spring":
@@ -437,26 +486,46 @@ class Runner:
     def launches_per_step(self):
         w = self.w
         # kernels of this library per step (memset nodes not counted):
-        # batched: one reset, then k_batch_sample + k_batch_finalize per
-        # iteration; BASES/VEGAS: grid reset (2), control (2), then
-        # k_sample + k_finish per pass; adjoint: k_grad + k_colsum
+        # batched: one reset, then per iteration the sampling kernels (FP32
+        # form: one per dimension present; otherwise one) and k_batch_finalize;
+        # BASES: grid reset (2), iteration set (1), control (2), then k_sample
+        # + k_finish per pass; VEGAS: grid reset (2), window reset (1),
+        # iteration set (1), control (1), then the passes; adjoint: k_grad +
+        # k_colsum
         if self.mode == "batched":
-            return 1 + 2 * w["itmx"]
+            per_it = len({i["ndim"] for i in self.insts}) if self.prec_name == "fp32" else 1
+            return 1 + (per_it + 1) * w["itmx"]
         if self.mode == "bases":
-            return 2 + 2 + 2 * (w["itmx1"] + w["itmx2"])
+            return 2 + 1 + 2 + 2 * (w["itmx1"] + w["itmx2"])
         if self.mode == "adjoint":
             return 2
         if self.mode == "spring":  # cube table and guide (5 kernels), trials, compaction
             return 7
-        return 2 + 2 + 2 * w["itmx"]
+        return 2 + 1 + 1 + 1 + 2 * w["itmx"]
+
+    def estimates(self, h):
+        """The results the step produced, as (I, sigma) pairs: one per
+        instance (batched), one for a VEGAS or BASES run; the adjoint's
+        estimate and gradient components with sigma None."""
+        gv = self.gv
+        if self.mode == "batched":
+            return [(r["I"], r["sigma"]) for r in gv.vegas_batch_iterate(h, 0)]
+        if self.mode == "adjoint":
+            g, I = gv.vegas_grad(h, 1000)
+            return [(I, None)] + [(v, None) for v in g]
+        if self.mode == "spring":
+            return []
+        r = gv.vegas_iterate(h, 0, refine=False)
+        return [(r["I"], r["sigma"])]
 
     def step(self, h):
         gv, w = self.gv, self.w
         if self.mode == "batched":
             gv.vegas_batch_reset(h)
             gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=False)
-        elif self.mode == "bases":
+        elif self.mode == "bases":  # every step from iteration 0: the same points
             gv.vegas_reset_grid(h)
+            gv.vegas_set_iteration(h, 0)
             gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0, result=False)
         elif self.mode == "adjoint":
             gv.vegas_grad(h, 1000)
@@ -465,6 +534,7 @@ class Runner:
         else:
             gv.vegas_reset_grid(h)
             gv.vegas_reset_results(h)
+            gv.vegas_set_iteration(h, 0)
             gv.vegas_iterate(h, w["itmx"], refine=True, result=False)
 
     def result(self, h):
@@ -489,7 +559,9 @@ class Runner:
         gv = self.gv
         if self.mode == "batched":
             p = gv.vegas_batch_profile(h, 5)
-            return "k_batch_sample", p["sample"], sum(i["ncall"] for i in self.insts), {"finalize_ms": p["finalize"]}
+            name = ("k_batch_dim (one kernel per dimension, concurrent)" if self.prec_name == "fp32"
+                    else "k_batch_sample")
+            return name, p["sample"], sum(i["ncall"] for i in self.insts), {"finalize_ms": p["finalize"]}
         if self.mode == "adjoint":
             import torch
             gv.vegas_grad(h, 1000)
@@ -536,8 +608,8 @@ class Runner:
     def launch(self, h):
         gv = self.gv
         if self.mode == "batched":
-            return gv.vegas_batch_get_launch(h)
-        return gv.vegas_get_launch(h)
+            return dict(gv.vegas_batch_get_launch(h), **gv.vegas_batch_get_tile(h))
+        return dict(gv.vegas_get_launch(h), **gv.vegas_get_tile(h))
 
     # ------------------------------------------------------------ end to end
     def e2e_step(self, h):
@@ -557,6 +629,8 @@ class Runner:
         gv.vegas_set_grid(h, edges0)
         gv.vegas_set_params(h, np.asarray(w["params"], dtype=np.float64))
         h2d = edges0.nbytes + 8 * (3 * 32 + 24)
+        if self.mode in ("bases", "vegas"):
+            gv.vegas_set_iteration(h, 0)
         if self.mode == "bases":
             gv.bases_integrate(h, w["itmx1"], 0.0, w["itmx2"], 0.0)
             return h2d, 160
@@ -569,6 +643,111 @@ class Runner:
 
     def close(self, h):
         h.close()
+
+
+def timed_steps(R, h, k, warm, flush, stream, dist=None):
+    """W untimed steps, then k steps each timed by CUDA events on the
+    library's stream, L2 flushed before each; barriers around (ranks)."""
+    import torch
+    for _ in range(warm):
+        R.step(h)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        R.step(h)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def roofline_of(R, h, peaks, peak_src, sms, workload):
+    """The roofline object of the dominant kernel (ALU-bound: algorithmic
+    operations per point x points per launch / its CUDA-event time, against
+    the FP32 lane-issue peak) and the other kernel timings."""
+    gv = R.gv
+    kname, kms, units, other = R.kernel_ms(h)
+    ops_pt = R.ops_per_point()
+    if not ops_pt:
+        return None, other
+    achieved = ops_pt * units / (kms * 1e-3) / 1e12
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    traffic = TRAFFIC.get(workload)
+    if traffic is not None and R.mode == "bases":  # launch-weighted like the time
+        traffic = (R.w["itmx1"] * traffic[0] + R.w["itmx2"] * traffic[1]) / (R.w["itmx1"] + R.w["itmx2"])
+    elif traffic is not None:
+        traffic = traffic[0]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kname, "ops_per_point": round(ops_pt, 1),
+            "points_per_launch": units, "ms_per_launch": kms,
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)"}
+    if R.precision() == gv.FP64:
+        roof["note"] = "FP64 form: bound by the FP64 pipe, see fp64_rate"
+    if "launch_kinds" in other:
+        roof["launch_kinds"] = other["launch_kinds"]
+    return roof, other
+
+
+def fp64_leg(R, h, flush, stream, rate32, steps):
+    """The plain FP64 GPU path of the same workload on the same points
+    (24-bit words, the same Philox iterations and, for the adjoint, the same
+    grid): its rate, the speed-up, and the largest difference of the two
+    forms' estimates in units of the FP64 sigma (relative for the adjoint)."""
+    gv = R.gv
+    h64 = R.make(gv.FP64)
+    if R.mode == "adjoint":
+        gv.vegas_set_grid(h64, gv.vegas_get_grid(h))
+    ms64 = timed_steps(R, h64, steps, 2, flush, stream)
+    e32, e64 = R.estimates(h), R.estimates(h64)
+    out = {"value": R.points_per_step * steps / (sum(ms64) / 1e3), "unit": UNIT, "steps": steps,
+           "same_points": True, "result": R.result(h64)}
+    out["speedup"] = rate32 / out["value"]
+    sig = [abs(a[0] - b[0]) / b[1] for a, b in zip(e32, e64) if b[1]]
+    rel = [abs(a[0] - b[0]) / abs(b[0]) for a, b in zip(e32, e64) if b[0]]
+    out["max_dI_over_sigma"] = max(sig) if sig else None
+    out["max_rel_dI"] = max(rel) if rel else None
+    if R.mode in ("bases", "vegas"):
+        # each form refines its own grid from its own per-bin sums, and
+        # refinement amplifies their FP32 rounding from iteration to
+        # iteration; on one grid and one iteration's points the two forms
+        # differ only by the FP32 arithmetic
+        gv.vegas_set_grid(h64, gv.vegas_get_grid(h))
+        I32, _ = gv.vegas_eval(h, 1000)
+        I64, v64 = gv.vegas_eval(h64, 1000)
+        out["same_grid"] = {"dI_over_sigma": abs(I32 - I64) / v64 ** 0.5 if v64 > 0 else None,
+                            "rel_dI": abs(I32 - I64) / abs(I64) if I64 else None,
+                            "note": "one pass at Philox iteration 1000 on the FP32 run's final grid"}
+    R.close(h64)
+    return out
+
+
+EXTRA_WORKLOADS = ("dgauss8", "rambo5", "rambo4_adjoint")
+
+
+def extra_line(name, gv, stream, flush, peaks, peak_src, sms, steps=10):
+    """Value, roofline fraction and FP64 speed-up of one more workload,
+    timed in the same run as the headline one."""
+    R = Runner(name, gv, stream, 0, None)
+    h = R.make(R.precision())
+    ms = timed_steps(R, h, steps, 3, flush, stream)
+    value = R.points_per_step * steps / (sum(ms) / 1e3)
+    roof, _ = roofline_of(R, h, peaks, peak_src, sms, name)
+    line = {"value": value, "unit": UNIT, "ms_per_step": sum(ms) / steps, "steps": steps,
+            "roofline_frac": roof["frac"] if roof else None, "dominant_kernel": roof["kernel"] if roof else None,
+            "kernel_ms_per_launch": roof["ms_per_launch"] if roof else None,
+            "launch": R.launch(h), "autotuned": R.tuned}
+    f = fp64_leg(R, h, flush, stream, value, 3)
+    line["fp64"] = {k: f[k] for k in ("value", "speedup", "max_dI_over_sigma", "max_rel_dI", "same_grid") if k in f}
+    line["result"] = R.result(h)
+    R.close(h)
+    return line
 
 
 def run_ours(args):
@@ -592,27 +771,9 @@ def run_ours(args):
     prec = R.precision()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def timed(h, k, warm):
-        for _ in range(warm):
-            R.step(h)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        for a, b in evs:
-            flush.zero_()
-            a.record(stream)
-            R.step(h)
-            b.record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        return [a.elapsed_time(b) for a, b in evs]
-
     h = R.make(prec)
     with ClockSampler(local) as clk:
-        step_ms = timed(h, args.steps, args.warmup)
+        step_ms = timed_steps(R, h, args.steps, args.warmup, flush, stream, dist)
     total_ms = max_over_ranks(sum(step_ms), dist)
     pps = R.points_per_step
     value = whole_job_rate(world, pps, args.steps, total_ms / 1e3)
@@ -621,26 +782,7 @@ def run_ours(args):
     # roofline of the dominant kernel, timed by CUDA events on its stream
     peaks, peak_src = _measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    kname, kms, units, other = R.kernel_ms(h)
-    ops_pt = R.ops_per_point()
-    roof = None
-    if ops_pt:
-        achieved = ops_pt * units / (kms * 1e-3) / 1e12
-        mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = sms * 128 * mhz * 1e6 / 1e12
-        traffic = TRAFFIC.get(args.workload)
-        if traffic is not None and R.mode == "bases":  # launch-weighted like the time
-            traffic = (R.w["itmx1"] * traffic[0] + R.w["itmx2"] * traffic[1]) / (R.w["itmx1"] + R.w["itmx2"])
-        elif traffic is not None:
-            traffic = traffic[0]
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kname, "ops_per_point": round(ops_pt, 1),
-                "points_per_launch": units, "ms_per_launch": kms,
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({peak_src} max clock)"}
-        if prec == gv.FP64:
-            roof["note"] = "FP64 form: bound by the FP64 pipe, see fp64_rate"
-        if "launch_kinds" in other:
-            roof["launch_kinds"] = other["launch_kinds"]
+    roof, other = roofline_of(R, h, peaks, peak_src, sms, args.workload)
     extra = dict(other)
     if R.mode in ("bases", "vegas"):
         launch = gv.vegas_get_launch(h)
@@ -655,12 +797,7 @@ def run_ours(args):
     # the plain FP64 GPU path on the same points (speed-up denominator)
     fp64 = None
     if not args.no_fp64 and prec != gv.FP64:
-        h64 = R.make(gv.FP64)
-        k64 = max(3, args.steps // 4)
-        ms64 = timed(h64, k64, 2)
-        fp64 = {"value": pps * k64 / (sum(ms64) / 1e3), "unit": UNIT, "steps": k64, "result": R.result(h64)}
-        fp64["speedup"] = (value / world) / fp64["value"]
-        R.close(h64)
+        fp64 = fp64_leg(R, h, flush, stream, value / world, max(3, args.steps // 4))
 
     # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
@@ -681,6 +818,18 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} SPRING trials on the same frozen grid and cube maxima, {dt:.1f} s "
                          "single-threaded FP64 C oracle"}
+    if rank == 0 and world == 1 and not args.no_cpu and R.mode == "batched":
+        rate, n, dt, k = oracle_rate_batched()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} points: one iteration of each of the first {k} instances of the batch on their "
+                         f"uniform grids, {dt:.1f} s single-threaded FP64 C oracle"}
+        try:
+            rate_p, n_p, dt_p, P = oracle_rate_batched_allcores()
+            cpu_all = {"value": rate_p, "unit": UNIT, "cores": P, "kind": "oracle, one process per core",
+                       "sample": f"{n_p} points: each of {P} processes one iteration of its own instances "
+                                 f"(every {P}th, about 2^21 points), slowest {dt_p:.1f} s"}
+        except Exception as e:  # the single-threaded line above stands on its own
+            cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu and R.mode in ("bases", "vegas"):
         bases = R.mode == "bases"
         rate, n, dt = oracle_rate(args.workload, 3, 3) if bases else oracle_rate(args.workload, 1, 0)
@@ -695,13 +844,25 @@ def run_ours(args):
         except Exception as e:  # the single-threaded line above stands on its own
             cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
 
+    # more workloads in the same run (one GPU)
+    workloads = None
+    if world == 1 and not args.no_extras and args.workload == "genz256":
+        workloads = {}
+        for name in EXTRA_WORKLOADS:
+            try:
+                workloads[name] = extra_line(name, gv, stream, flush, peaks, peak_src, sms)
+            except Exception as e:  # one failing extra does not hide the headline
+                workloads[name] = {"error": f"{type(e).__name__}: {e}"}
+
     clocks = clk.summary()
     if rank == 0:
+        accumulation = {"fp32": "fp32_compensated", "fp32_acc64": "fp32_values_fp64_sums",
+                        "fp64": "fp64"}[R.prec_name]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != gv.FP64 else "f64",
-            "data": "synthetic", "config": dict(_config(args.workload), accumulation=R.prec_name,
+            "data": "synthetic", "config": dict(_config(args.workload), accumulation=accumulation,
                                                 launch=R.launch(h)),
             "roofline": roof, **extra, "fp64_path": fp64, "cpu_baseline": cpu,
             "cpu_baseline_allcores": cpu_all,
@@ -709,6 +870,8 @@ def run_ours(args):
             "result": res,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         }
+        if workloads is not None:
+            line["workloads"] = workloads
         if R.tuned:
             line["config"]["autotuned"] = R.tuned
         print(json.dumps(line))
@@ -749,12 +912,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dgauss8",
+    ap.add_argument("--workload", default="genz256",
                     choices=["dgauss8", "gauss4", "rambo5", "rambo4_adjoint", "genz256", "spring_dgauss8",
                              "user_dgauss8", "wmunu"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp32_acc64", "fp64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time only the chosen workload (the default genz256 run also times dgauss8, rambo5 and "
+                         "rambo4_adjoint)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler runs, where the autotuner's timings are skewed)")
     ap.add_argument("--launch", default=None, metavar="THREADS,PPT",

@@ -245,8 +245,10 @@ vegas_status vegas_get_history(vegas_ctx* ctx, double* hist, int max_iters,
  * (sum w, sum w^2); VEGAS_ESTATE without stratification. */
 vegas_status vegas_get_cube_sums(vegas_ctx* ctx, double* sums);
 
-/* The Philox iteration counter (iterations run so far) and a setter for
- * exact resume together with vegas_set_grid. */
+/* The Philox iteration counter (iterations run so far; synchronises the
+ * stream) and a setter for exact resume together with vegas_set_grid
+ * (stream-ordered on the device, no synchronisation; the next iteration
+ * draws iteration `it`'s points). */
 vegas_status vegas_get_iteration(vegas_ctx* ctx, uint32_t* it);
 vegas_status vegas_set_iteration(vegas_ctx* ctx, uint32_t it);
 

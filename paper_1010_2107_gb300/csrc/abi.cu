@@ -564,7 +564,7 @@ vegas_status get_graph(vegas_ctx* c, int shape, int n1, int n2, int refine, doub
   vegas_status st = VEGAS_OK;
   auto ctl = [&](int ops, double acc) {
     if (st) return;
-    cudaError_t e = gv_launch_control(c->d_st, ops, acc, c->stream);
+    cudaError_t e = gv_launch_control(c->d_st, ops, acc, 0u, c->stream);
     if (e != cudaSuccess) st = c->fail(VEGAS_ECUDA, "control: %s", cudaGetErrorString(e));
   };
   if (shape == 0) {
@@ -906,7 +906,7 @@ vegas_status vegas_iterate(vegas_ctx* c, int n_iter, int refine, vegas_result* o
 
 vegas_status vegas_reset_results(vegas_ctx* c) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  CK(c, gv_launch_control(c->d_st, gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, c->cfg.acc, c->stream));
+  CK(c, gv_launch_control(c->d_st, gv::CTL_RESET_WINDOW | gv::CTL_SET_ACC, c->cfg.acc, 0u, c->stream));
   c->hist_upper = 0;
   return VEGAS_OK;
 }
@@ -1176,11 +1176,7 @@ vegas_status vegas_get_iteration(vegas_ctx* c, uint32_t* it) {
 
 vegas_status vegas_set_iteration(vegas_ctx* c, uint32_t it) {
   if (!c) return thread_fail(VEGAS_EINVAL, "ctx is NULL");
-  vegas_status st = read_state(c);
-  if (st) return st;
-  c->h_st->it = it;
-  CK(c, cudaMemcpyAsync(&c->d_st->it, &c->h_st->it, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
+  CK(c, gv_launch_control(c->d_st, gv::CTL_SET_ITER, 0.0, it, c->stream));
   return VEGAS_OK;
 }
 

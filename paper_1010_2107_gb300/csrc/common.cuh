@@ -222,7 +222,7 @@ struct GState {
 constexpr int kFinishThreads = 256;
 
 // Device-side control operations captured into the iteration graphs.
-enum { CTL_RESET_WINDOW = 1, CTL_SET_ACC = 2, CTL_SNAPSHOT = 4 };
+enum { CTL_RESET_WINDOW = 1, CTL_SET_ACC = 2, CTL_SNAPSHOT = 4, CTL_SET_ITER = 8 };
 
 // Arguments of the sampling kernel (steps 2-4).
 struct SampleArgs {

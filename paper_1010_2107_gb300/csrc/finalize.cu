@@ -197,8 +197,10 @@ __global__ void __launch_bounds__(256) k_colsum(const double* part, int ncols, i
   if (lane == 0) out[col] = acc;
 }
 
-// Window / stop-flag bookkeeping between passes (one thread).
-__global__ void k_control(GState* st, int ops, double acc) {
+// Window / stop-flag bookkeeping between passes (one thread); CTL_SET_ITER
+// sets the Philox iteration counter.
+__global__ void k_control(GState* st, int ops, double acc, uint32_t it) {
+  if (ops & CTL_SET_ITER) st->it = it;
   if (ops & CTL_SNAPSHOT) {
     st->ph1_I = st->I;
     st->ph1_sigma = st->sigma;
@@ -287,8 +289,8 @@ cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* o
   return cudaGetLastError();
 }
 
-cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s) {
-  gv::k_control<<<1, 1, 0, s>>>(st, ops, acc);
+cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, uint32_t it, cudaStream_t s) {
+  gv::k_control<<<1, 1, 0, s>>>(st, ops, acc, it);
   return cudaGetLastError();
 }
 

@@ -200,7 +200,7 @@ const void* gv_batch_dim_kernel_lo(int d, int pif);
 const void* gv_batch_dim_kernel_hi(int d, int pif);
 cudaError_t gv_launch_finish(const gv::FinArgs* F, cudaStream_t s);
 cudaError_t gv_launch_colsum(const double* part, int ncols, int nrows, double* out, cudaStream_t s);
-cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, cudaStream_t s);
+cudaError_t gv_launch_control(gv::GState* st, int ops, double acc, uint32_t it, cudaStream_t s);
 cudaError_t gv_launch_uniform_grid(double* edges, int d, int N, cudaStream_t s);
 cudaError_t gv_launch_tables(const double* edges, int d, int N, double2* t64, float2* t32,
                              cudaStream_t s);

@@ -206,7 +206,14 @@ struct TileHist {
   static constexpr bool COMP = ACC == 2;
   static constexpr int V = 16 / (int)sizeof(H);  // slots per 16-byte vector
   using HV = typename std::conditional<sizeof(H) == 4, float4, double2>::type;
-  static __host__ __device__ int stride(int cap) { return cap + V; }
+  // cap slots and a spare vector, padded to an odd number of 16-byte
+  // vectors: the rows of consecutive cells then start in all eight vector
+  // positions of the 32 banks (conflict-free vector reads in the gather)
+  static __host__ __device__ int stride(int cap) {
+    int s = cap + V;
+    while ((s / V) % 2 == 0) s += V;
+    return s;
+  }
   static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
   static __host__ __device__ size_t off_bucket(int dN) { return a16((size_t)dN * sizeof(int)); }
   static __host__ __device__ size_t off_cta(int dN, int cap) {
