@@ -191,21 +191,27 @@ __device__ __forceinline__ void dim_scatter(int* cnt, float* rows, float* junk, 
 
 // End of a tile (all threads): each cell's bucket into its FP32 (S1, S2)
 // tile sums (paired instructions), optionally folded into the item's second
-// level ff; the vectors read are cleared and the counter reset.
-__device__ __forceinline__ void dim_gather(int* cnt, float* rows, float2* cc, float2* ff, int dN, int S, int cap,
-                                           bool fold) {
+// level ff, and the counter reset.  Only the filled slots are read: whole
+// vectors, then the partial last one with its stale slots masked (the
+// slots are never cleared: shared-memory stores are the scarce resource).
+__device__ __forceinline__ void dim_gather(int* cnt, const float* rows, float2* cc, float2* ff, int dN, int S,
+                                           int cap, bool fold) {
   __syncthreads();
   for (int cell = threadIdx.x; cell < dN; cell += blockDim.x) {
-    const int nq = (min(cnt[cell], cap) + 3) >> 2;
-    float4* row = reinterpret_cast<float4*>(rows + cell * S);
+    const int n = min(cnt[cell], cap);
+    const float4* row = reinterpret_cast<const float4*>(rows + cell * S);
     float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-    for (int q = 0; q < nq; ++q) {
-      const float4 v = row[q];
-      row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto add = [&](const float4 v) {
       const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
       s1 = __fadd2_rn(s1, __fadd2_rn(lo, hi));
       s2 = __ffma2_rn(lo, lo, s2);
       s2 = __ffma2_rn(hi, hi, s2);
+    };
+    const int nf = n >> 2, r = n & 3;
+    for (int q = 0; q < nf; ++q) add(row[q]);
+    if (r) {
+      const float4 v = row[nf];
+      add(make_float4(v.x, r > 1 ? v.y : 0.f, r > 2 ? v.z : 0.f, 0.f));
     }
     float2 c = cc[cell];
     c.x += s1.x + s1.y;
@@ -287,11 +293,9 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
   __shared__ fpair red_p[8][2];
   __shared__ int red_n[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  {  // counters and bucket rows start cleared; every gather leaves them so
-    float4* b4 = reinterpret_cast<float4*>(rows);
-    for (int i = tid; i < cells * S / 4; i += blockDim.x) b4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = tid; i < cells; i += blockDim.x) cnt[i] = 0;
-  }
+  // counters start at zero and every gather leaves them so; the bucket
+  // slots need no clearing (a gather reads only the filled ones)
+  for (int i = tid; i < cells; i += blockDim.x) cnt[i] = 0;
   int cur = -1;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(R.head, 1);
