@@ -65,8 +65,9 @@ ALGO_OPS = {
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/), per pass kind (refining, frozen grid); a workload
 # whose kernel changed since its capture has no entry.
-TRAFFIC = {"dgauss8": (81152, 612608), "wmunu": (79104, 350976), "rambo4_adjoint": (1298688,),
-           "spring_dgauss8": (1008640 + 4173312,)}
+TRAFFIC = {"dgauss8": (84864, 615424), "rambo5": (113792,),
+           # one batched pass: the sum over its fifteen dimension kernels
+           "genz256": (3019776,)}
 
 
 def _workload(name):
