@@ -129,11 +129,15 @@ def test_fp32_iteration_vs_oracle(gv, orc, name, kind, d, params, kw, precision)
         _, bins = gv.vegas_get_grid(ctx, bin_sums=True)
     o = orc.iteration(cfg, fn, orc.uniform_grid(d, 50), 2)
     sig = math.sqrt(o["var"])
-    assert abs(I - o["I"]) <= 1e-5 * abs(o["I"]) + 1e-300 or kind == wl.GENZ_OSCILLATORY
-    assert abs(I - o["I"]) <= 0.1 * sig + 1e-300
-    assert abs(math.sqrt(var) - sig) <= 1e-3 * sig + 1e-300
     p = orc.sample_batch(cfg, orc.uniform_grid(d, 50), 2, np.arange(ncall))
     absw = np.abs(orc.integrand(fn, p["x"]) * p["jac"])
+    # 1e-5 of the larger of |I| and the mean |w|: the same as 1e-5 of |I|
+    # for the non-negative integrands; for the sign-changing oscillatory
+    # family, whose |I| can sit far below the weights it cancels, the
+    # condition-scaled form of the bar
+    assert abs(I - o["I"]) <= 1e-5 * max(abs(o["I"]), absw.mean()) + 1e-300
+    assert abs(I - o["I"]) <= 0.1 * sig + 1e-300
+    assert abs(math.sqrt(var) - sig) <= 1e-3 * sig + 1e-300
     assert _cond_close(bins[0], o["S1"], absw.sum(), 1e-5)
     # S2: also within twice the per-point FP32 bar (1e-4) of the cell itself
     assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-5 * (absw ** 2).sum() + 2e-4 * np.abs(o["S2"]))
