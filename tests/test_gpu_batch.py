@@ -5,7 +5,14 @@ workload against closed forms.
 Bars: FP64, iteration estimates within 1e-12 relative of the standalone
 context and refined grids within 1e-12; compensated FP32, within 1e-5
 relative and 0.1 sigma; the oracle loop on the same points (FP64) within
-1e-12; every Genz instance within 5 sigma of its closed form."""
+1e-12; every Genz instance within 5 sigma of its closed form.  The FP32
+per-dimension kernels against the oracle's first iteration, instance by
+instance (d = 1..16, every family, 2 to 256 bins, one or two points in
+flight, and sampled instances of the full 256-instance batch in the
+benchmarked shape): I within 1e-5 of max(|I|, mean |w|) and 0.1 sigma,
+S1 within 1e-5 sum|w|, S2 within 1e-5 sum w^2 + 2e-4 of the cell, with
+the weights of points within FP32 rounding of a discontinuity (oracle cut
+margin below 1e-4) allowed on top."""
 import math
 
 import numpy as np
@@ -101,3 +108,106 @@ def test_genz256_workload_against_closed_forms(gv):
         checked += 1
         assert abs(r["I"] - exact) <= 5 * r["sigma"] + 1e-12 * abs(exact), (ins["kind"], ins["ndim"], r, exact)
     assert checked > 150
+
+
+def _family_params(kind, d, rng):
+    """Parameters of one Genz-family (or two-peak Gaussian) instance: the
+    layouts of vegas_create's parameter block."""
+    a = rng.uniform(0.5, 3.0, d)
+    u = rng.uniform(0.2, 0.8, d)
+    if kind in (wl.GENZ_GAUSSIAN, wl.GENZ_PRODUCT_PEAK, wl.GENZ_CONTINUOUS):
+        return list(np.concatenate([a, u]))
+    if kind == wl.GENZ_CORNER_PEAK:
+        return list(a / d)
+    if kind == wl.GENZ_OSCILLATORY:
+        return list(np.concatenate([a, u[:1]]))
+    if kind == wl.GENZ_DISCONTINUOUS:
+        return list(np.concatenate([a / d, u[:2]]))
+    return [0.3, 0.7, 0.1]  # two-peak Gaussian: centres and width
+
+
+def _weights_abs(orc, cfg, fn, edges, it, n, chunk=1 << 18):
+    """Sum of |w| over the n points of an iteration, and the sums of |w| and
+    w^2 over the points within FP32 rounding of a discontinuity (cut margin
+    below 1e-4), which may fall on its other side (the oracle, in chunks)."""
+    tot, near1, near2 = 0.0, 0.0, 0.0
+    for s0 in range(0, n, chunk):
+        p = orc.sample_batch(cfg, edges, it, np.arange(s0, min(n, s0 + chunk)))
+        w = orc.integrand(fn, p["x"]) * p["jac"]
+        tot += np.abs(w).sum()
+        near = orc.cut_margin(fn, p["x"]) < 1e-4
+        near1 += np.abs(w[near]).sum()
+        near2 += (w[near] ** 2).sum()
+    return tot, near1, near2
+
+
+def _check_first_iteration(gv, orc, b, i, ins, N, seed):
+    """Instance i of a batch after one refining iteration against the
+    oracle's iteration 0 on the uniform grid (FP32 bars: I within 1e-5 of
+    max(|I|, mean |w|) and 0.1 sigma, S1 within 1e-5 sum|w|, S2 within
+    1e-5 sum w^2 + 2e-4 of the cell)."""
+    d = ins["ndim"]
+    cfg = orc.make_cfg(d, nbins=N, ncall=ins["ncall"], ybits=24, seed=seed, instance=ins["instance"])
+    fn = orc.Integrand(ins["kind"], d, ins["params"])
+    e0 = orc.uniform_grid(d, N)
+    o = orc.iteration(cfg, fn, e0, 0)
+    absw, near1, near2 = _weights_abs(orc, cfg, fn, e0, 0, ins["ncall"])
+    hist = gv.vegas_batch_get_history(b, i)
+    _, bins = gv.vegas_batch_get_grid(b, i, bin_sums=True)
+    I, var = hist[0]
+    sig = math.sqrt(o["var"])
+    n = ins["ncall"]
+    assert abs(I - o["I"]) <= 1e-5 * max(abs(o["I"]), absw / n) + near1 / n + 1e-300, (ins, I, o["I"])
+    assert abs(I - o["I"]) <= 0.1 * sig + near1 / n + 1e-300, (ins, I, o["I"], sig)
+    assert np.all(np.abs(bins[0] - o["S1"]) <= 1e-5 * absw + near1), ins
+    sw2 = o["S2"][0].sum()  # every point lands in one bin of an axis
+    assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-5 * sw2 + 2e-4 * np.abs(o["S2"]) + near2), ins
+
+
+FAMILIES = [wl.GENZ_GAUSSIAN, wl.GENZ_PRODUCT_PEAK, wl.GENZ_CORNER_PEAK, wl.GENZ_OSCILLATORY,
+            wl.GENZ_CONTINUOUS, wl.GENZ_DISCONTINUOUS, wl.DOUBLE_GAUSSIAN]
+
+
+@pytest.mark.parametrize("N", [2, 37, 256])
+@pytest.mark.parametrize("pif", [1, 2])
+def test_batch_dimension_kernels_against_the_oracle(gv, orc, N, pif):
+    """The FP32 batched pass (one kernel per exact dimension, d = 1..16, every
+    family, ragged point counts, 2 to 256 bins: tiles from heavy bucket
+    overflow to sparse) against the oracle's first iteration, instance by
+    instance."""
+    rng = np.random.default_rng(100 + N + pif)
+    insts = []
+    for d in range(1, 17):
+        kind = FAMILIES[d % len(FAMILIES)]
+        if kind == wl.GENZ_DISCONTINUOUS and d < 2:
+            kind = wl.GENZ_GAUSSIAN
+        insts.append(dict(kind=kind, ndim=d, params=_family_params(kind, d, rng), ncall=3001 + 977 * d + (d % 3),
+                          instance=10 + d))
+    with gv.vegas_batch_create(insts, nbins=N, precision=2, ybits=24, seed=6) as b:
+        gv.vegas_batch_set_launch(b, 128, 8)
+        gv.vegas_batch_set_tile(b, pif)
+        gv.vegas_batch_iterate(b, 1)
+        for i, ins in enumerate(insts):
+            _check_first_iteration(gv, orc, b, i, ins, N, 6)
+
+
+def test_genz256_first_iteration_against_the_oracle_in_the_benchmarked_shape(gv, orc):
+    """The full 256-instance batch (about 2.5e8 points) in the launch shape the
+    benchmark times (256 threads, 64 rounds, two points in flight): the first
+    iteration of sampled instances, one of every dimension present with at
+    most 2^20 points and the largest one, against the oracle."""
+    spec = wl.GENZ256
+    insts = wl.genz_batch(spec["count"], spec["seed"])
+    pick = {}
+    for i, ins in enumerate(insts):
+        if ins["ncall"] <= 1 << 20 and ins["ndim"] not in pick:
+            pick[ins["ndim"]] = i
+    big = max(range(len(insts)), key=lambda i: insts[i]["ncall"] * insts[i]["ndim"])
+    chosen = sorted(set(pick.values()) | {big})
+    with gv.vegas_batch_create(insts, nbins=spec["nbins"], precision=2, ybits=24, seed=spec["sample_seed"]) as b:
+        gv.vegas_batch_set_launch(b, 256, 64)
+        gv.vegas_batch_set_tile(b, 2)
+        gv.vegas_batch_iterate(b, 1)
+        for i in chosen:
+            _check_first_iteration(gv, orc, b, i, insts[i], spec["nbins"], spec["sample_seed"])
+    assert len(chosen) >= 10
