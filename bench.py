@@ -623,9 +623,18 @@ class Runner:
         import numpy as np
         gv, w = self.gv, self.w
         if self.mode == "batched":
+            # every instance's parameter block from host memory (the library
+            # derives the integrand constants and uploads them, 120 doubles
+            # per instance), then the run from uniform grids
+            if getattr(self, "_param_rows", None) is None:
+                width = max(len(i["params"]) for i in self.insts)
+                self._param_rows = np.zeros((len(self.insts), width))
+                for j, ins in enumerate(self.insts):
+                    self._param_rows[j, :len(ins["params"])] = ins["params"]
+            gv.vegas_batch_set_params(h, self._param_rows)
             gv.vegas_batch_reset(h)
             gv.vegas_batch_iterate(h, w["itmx"], refine=True, result=True)
-            return 0, 48 * len(self.insts) + 1200 * len(self.insts)
+            return 8 * (3 * 32 + 24) * len(self.insts), 48 * len(self.insts) + 1200 * len(self.insts)
         d, N = w["ndim"], w["nbins"]
         if self.mode == "spring":  # events copied to pinned host memory; the frozen grid stays
             r = gv.spring_generate(h, 0, w["ntrials"], events=True, out_x=self._pinned[0], out_t=self._pinned[1])

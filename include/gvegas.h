@@ -419,9 +419,10 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
                                 vegas_batch** out);
 void vegas_batch_destroy(vegas_batch* batch);
 
-/* Steps 2-6 of Sec. 2.1 for every instance, n_iter times (0..64): one
- * persistent sampling kernel and one finalisation kernel per iteration,
- * the whole call one CUDA graph; refining after each iteration when
+/* Steps 2-6 of Sec. 2.1 for every instance, n_iter times (0..64): per
+ * iteration the persistent sampling kernels (the FP32 form with 24-bit
+ * words: one per dimension present, run concurrently; otherwise one) and
+ * one finalisation kernel, the whole call one CUDA graph; refining after each iteration when
  * refine != 0.  out (nullable, host array of n) receives one result per
  * instance (combined over the instance's window) and forces a
  * synchronisation.  No ACC stop (every instance runs n_iter). */
@@ -429,6 +430,18 @@ vegas_status vegas_batch_iterate(vegas_batch* batch, int n_iter, int refine, veg
 
 /* Uniform grids, empty windows and iteration counters back to zero. */
 vegas_status vegas_batch_reset(vegas_batch* batch);
+
+/* Replace the integrand parameters of instances first .. first+count-1
+ * (Sec. 2.1 step 3, the integrand each instance's loop samples; the
+ * batched form of vegas_set_params).  params: host array; instance
+ * first + j reads its parameter block (the layout and count of
+ * vegas_create) from params + j * stride, so stride must be at least the
+ * largest count in the range.  The derived constants are formed on the
+ * host and uploaded in one stream-ordered copy from pinned memory; grids,
+ * histories and captured graphs are kept (the kernels read the constants
+ * at run time).  VEGAS_EINVAL, with nothing changed, for a range outside
+ * the batch, a short stride or parameters the instance's kind rejects. */
+vegas_status vegas_batch_set_params(vegas_batch* batch, int first, int count, const double* params, int stride);
 
 /* Grid edges [ndim_i][nbins+1] and (nullable) per-bin sums of the last
  * iteration [2][ndim_i][nbins] of instance i; its history (I_j, sigma_j^2). */

@@ -382,6 +382,7 @@ struct vegas_batch {
   BatchState* d_st = nullptr;
   int* d_head = nullptr;
   BatchState* h_st = nullptr;
+  double* h_derived = nullptr;  // pinned staging of vegas_batch_set_params
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
@@ -660,6 +661,7 @@ void vegas_batch_destroy(vegas_batch* b) {
   cudaFree(b->d_st);
   cudaFree(b->d_head);
   if (b->h_st) cudaFreeHost(b->h_st);
+  if (b->h_derived) cudaFreeHost(b->h_derived);
   for (int i = 0; i < vegas_batch::kAux; ++i) {
     if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
     if (b->join[i]) cudaEventDestroy(b->join[i]);
@@ -892,6 +894,35 @@ vegas_status vegas_batch_get_history(vegas_batch* b, int i, double* hist, int ma
   const int n = std::min(b->h_st[i].nhist, std::max(0, max_iters));
   if (n_out) *n_out = b->h_st[i].nhist;
   if (hist && n > 0) memcpy(hist, b->h_st[i].hist, sizeof(double) * 2 * n);
+  return VEGAS_OK;
+}
+
+vegas_status vegas_batch_set_params(vegas_batch* b, int first, int count, const double* params, int stride) {
+  if (!b) return bfail("batch is NULL");
+  if (first < 0 || count < 1 || first > b->n - count || !params)
+    return b->fail(VEGAS_EINVAL, "instances %d..%d outside the batch of %d, or params NULL", first, first + count - 1,
+                   b->n);
+  constexpr int K = gv::kNumDerived;
+  std::vector<double> dv((size_t)count * K, 0.0);
+  for (int j = 0; j < count; ++j) {
+    const int i = first + j;
+    const int np = (int)b->params[i].size();
+    if (np > stride) return b->fail(VEGAS_EINVAL, "stride %d below the %d parameters of instance %d", stride, np, i);
+    double scale = 1.0;
+    std::string why;
+    if (!gv::derive_params(b->kind[i], b->d[i], params + (size_t)j * stride, &dv[(size_t)j * K], &scale, &why))
+      return b->fail(VEGAS_EINVAL, "instance %d: %s", i, why.c_str());
+  }
+  if (!b->h_derived) BK(b, gv_malloc_host(&b->h_derived, b->derived.size() * sizeof(double)));
+  BK(b, cudaStreamSynchronize(b->stream));  // the staging's previous upload has left it
+  for (int j = 0; j < count; ++j) {
+    const double* p = params + (size_t)j * stride;
+    b->params[first + j].assign(p, p + b->params[first + j].size());
+  }
+  std::copy(dv.begin(), dv.end(), b->derived.begin() + (size_t)first * K);
+  std::copy(dv.begin(), dv.end(), b->h_derived + (size_t)first * K);
+  BK(b, cudaMemcpyAsync(b->d_derived + (size_t)first * K, b->h_derived + (size_t)first * K, dv.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, b->stream));
   return VEGAS_OK;
 }
 

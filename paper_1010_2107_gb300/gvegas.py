@@ -118,6 +118,7 @@ _SIGS = {
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP]),
     "vegas_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "vegas_batch_set_params": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_int]),
     "vegas_batch_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "vegas_batch_profile": (ctypes.c_int, [_P, ctypes.c_int, _DP]),
     "vegas_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -514,6 +515,20 @@ def vegas_batch_iterate(b: Batch, n_iter: int, refine: bool = True, result: bool
 
 def vegas_batch_reset(b: Batch):
     _bcheck(lib().vegas_batch_reset(b.handle), b.handle)
+
+
+def vegas_batch_set_params(b: Batch, params, first: int = 0):
+    """New parameter blocks for instances first, first+1, ...: a 2-D array
+    (one row per instance, rows at least as long as each block) or a list
+    of 1-D blocks."""
+    if isinstance(params, np.ndarray) and params.ndim == 2:
+        a = np.ascontiguousarray(params, dtype=np.float64)
+    else:
+        rows = [np.asarray(p, dtype=np.float64).ravel() for p in params]
+        a = np.zeros((len(rows), max((len(r) for r in rows), default=0)))
+        for j, r in enumerate(rows):
+            a[j, :len(r)] = r
+    _bcheck(lib().vegas_batch_set_params(b.handle, int(first), int(a.shape[0]), _dp(a), int(a.shape[1])), b.handle)
 
 
 def vegas_batch_get_grid(b: Batch, i: int, bin_sums: bool = False):

@@ -97,6 +97,7 @@ def test_null_arguments(gvlib):
     assert L.vegas_iterate(None, 1, 1, None) == gv.EINVAL
     assert L.vegas_get_grid(None, None, None) == gv.EINVAL
     assert L.bases_integrate(None, 1, 0.0, 1, 0.0, None, None) == gv.EINVAL
+    assert L.vegas_batch_set_params(None, 0, 1, None, 1) == gv.EINVAL
     L.vegas_destroy(None)
     assert isinstance(gv.vegas_last_error(None), str)
 

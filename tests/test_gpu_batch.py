@@ -211,3 +211,38 @@ def test_genz256_first_iteration_against_the_oracle_in_the_benchmarked_shape(gv,
         for i in chosen:
             _check_first_iteration(gv, orc, b, i, insts[i], spec["nbins"], spec["sample_seed"])
     assert len(chosen) >= 10
+
+
+@pytest.mark.parametrize("precision,ybits", [(0, 53), (2, 24)])
+def test_batch_set_params_matches_a_batch_created_with_them(gv, precision, ybits):
+    """vegas_batch_set_params on a batch whose iteration graph is already
+    captured, for a range of instances, gives the run of a batch created
+    with the new parameters (first iteration identical, the next within the
+    run-to-run reproducibility of the per-bin sums); a short stride or a
+    range outside the batch is refused with nothing changed."""
+    new = [dict(ins) for ins in SMALL]
+    for ins in new[1:4]:
+        p = np.asarray(ins["params"], dtype=float)
+        ins["params"] = list(p * 1.1) if ins["kind"] != wl.GENZ_OSCILLATORY else list(p + 0.05)
+    with gv.vegas_batch_create(SMALL, precision=precision, ybits=ybits, seed=4) as b1, \
+            gv.vegas_batch_create(new, precision=precision, ybits=ybits, seed=4) as b2:
+        for b in (b1, b2):
+            gv.vegas_batch_set_launch(b, 128, 16)
+        gv.vegas_batch_iterate(b1, 2)  # captures the two-iteration graph
+        rows = [ins["params"] for ins in new[1:4]]
+        with pytest.raises(gv.VegasError):
+            gv.vegas_batch_set_params(b1, rows, first=len(SMALL) - 2)  # runs past the end
+        short = np.zeros((3, 1))
+        with pytest.raises(gv.VegasError):
+            gv.vegas_batch_set_params(b1, short, first=1)
+        gv.vegas_batch_set_params(b1, rows, first=1)
+        for b in (b1, b2):
+            gv.vegas_batch_reset(b)
+            gv.vegas_batch_iterate(b, 2)
+        tol = 1e-12 if precision == 0 else 1e-5
+        for i in range(len(SMALL)):
+            h1, h2 = gv.vegas_batch_get_history(b1, i), gv.vegas_batch_get_history(b2, i)
+            assert h1[0, 0] == h2[0, 0] and h1[0, 1] == h2[0, 1], i
+            np.testing.assert_allclose(h1[1], h2[1], rtol=tol)
+            np.testing.assert_allclose(gv.vegas_batch_get_grid(b1, i), gv.vegas_batch_get_grid(b2, i), rtol=0,
+                                       atol=1e-12 if precision == 0 else 1e-5)
