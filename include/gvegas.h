@@ -403,7 +403,11 @@ vegas_status vegas_profile_frozen_pass(vegas_ctx* ctx, int n_pass, double* ms);
  * (1..16), ncall (< 2^32), alpha and `instance` id (Philox counter word 3,
  * so instance i draws the points a standalone context with the same id
  * draws).  No stratification and no ACC stop.  The stream of cfgs[0] (or a
- * stream the batch creates) orders all work.
+ * stream the batch creates) orders all work.  Shared memory: the FP32 form
+ * with 24-bit words runs one kernel per dimension and takes every nbins up
+ * to GVEGAS_MAXBINS; the other forms run one kernel sized for the widest
+ * instance, so nbins times the widest ndim is limited to about 2750
+ * (256 bins up to 10 axes, 172 bins at 16 axes), VEGAS_EINVAL beyond.
  * ------------------------------------------------------------------------ */
 typedef struct vegas_batch vegas_batch;
 

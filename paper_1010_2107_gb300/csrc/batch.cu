@@ -86,9 +86,11 @@ __device__ __forceinline__ void batch_item_points(const BatchArgs& B, const Samp
 template <typename T, int ACC>
 struct BatchSmem {
   static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
-  static __host__ __device__ size_t params(int N) { return (size_t)kBatchDM * N * sizeof(typename Vec2<T>::type); }
-  static __host__ __device__ size_t hist(int N) { return a16(params(N) + kNumDerived * sizeof(T)); }
-  static __host__ __device__ size_t total(int N, int cap) { return hist(N) + TileHist<ACC>::bytes(kBatchDM * N, cap); }
+  static __host__ __device__ size_t params(int md, int N) { return (size_t)md * N * sizeof(typename Vec2<T>::type); }
+  static __host__ __device__ size_t hist(int md, int N) { return a16(params(md, N) + kNumDerived * sizeof(T)); }
+  static __host__ __device__ size_t total(int md, int N, int cap) {
+    return hist(md, N) + TileHist<ACC>::bytes(md * N, cap);
+  }
 };
 
 template <typename T, int ACC, int YB>
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   constexpr bool COMP = ACC == 2;
   extern __shared__ __align__(16) unsigned char smem[];
   T2* tab = reinterpret_cast<T2*>(smem);
-  T* P = reinterpret_cast<T*>(smem + L::params(B.N));
+  T* P = reinterpret_cast<T*>(smem + L::params(B.maxd, B.N));
   __shared__ int s_item;
   __shared__ double red_d[8][3];
   __shared__ fpair red_p[8][2];
@@ -122,10 +124,11 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   for (int i = 0; i < kPhiloxKeyWords; ++i) A.ks[i] = B.ks[i];
   A.inv_gb_d = 1.0 / (double)(1ull << YB);
   A.inv_gb_f = (float)A.inv_gb_d;
-  // one layout for every instance (sized for kBatchDM axes); the bucket
+  // one layout for every instance (sized for the widest); the bucket
   // slots are cleared once and every gather leaves them cleared
-  hist.bind(smem + L::hist(N), kBatchDM * N, N, B.cap, B.ppt, kBatchDM * N);
-  hist.zero_buckets(tid, blockDim.x, kBatchDM * N);
+  const int MD = B.maxd;
+  hist.bind(smem + L::hist(MD, N), MD * N, N, B.cap, B.ppt, MD * N);
+  hist.zero_buckets(tid, blockDim.x, MD * N);
 
   for (;;) {
     if (tid == 0) s_item = atomicAdd(B.head, 1);
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
       for (int i = tid; i < kNumDerived; i += blockDim.x) P[i] = (T)dp[i];
       cur = W.inst;
     }
-    hist.bind(smem + L::hist(N), dN, N, B.cap, B.ppt, kBatchDM * N);
+    hist.bind(smem + L::hist(MD, N), dN, N, B.cap, B.ppt, MD * N);
     hist.zero(tid, blockDim.x);
     __syncthreads();
     A.d = d;
@@ -341,6 +344,7 @@ thread_local std::string g_batch_err;
 
 struct vegas_batch {
   int n = 0, N = 50, prec = VG_FP32_ACCCOMP, ybits = 24;
+  int maxd = 1;  // widest instance
   uint64_t seed = 1;
   std::vector<vegas_config> cfg;
   std::vector<int> kind, d;
@@ -430,8 +434,8 @@ const void* pick_batch_kernel(int prec, int ybits) {
   return ybits == 24 ? batch_kernel<float, 2, 24>() : batch_kernel<float, 2, 53>();
 }
 
-size_t batch_smem(int prec, int N, int cap) {
-  return prec == VG_FP64 ? gv::BatchSmem<double, 0>::total(N, cap) : gv::BatchSmem<float, 2>::total(N, cap);
+size_t batch_smem(int prec, int md, int N, int cap) {
+  return prec == VG_FP64 ? gv::BatchSmem<double, 0>::total(md, N, cap) : gv::BatchSmem<float, 2>::total(md, N, cap);
 }
 
 // Items of `threads * rounds` points, instances in decreasing NCALL order so
@@ -544,7 +548,7 @@ vegas_status configure(vegas_batch* b) {
                              (int)cudaSharedmemCarveoutMaxShared));
   cudaError_t e = cudaSuccess;
   auto occ_of = [&](int cap, int) -> int {
-    const size_t smem = batch_smem(b->prec, b->N, cap);
+    const size_t smem = batch_smem(b->prec, b->maxd, b->N, cap);
     int o = 0;
     if (e != cudaSuccess || smem > 227 * 1024) return 0;
     e = gv_raise_smem_limit(b->kernel, smem);
@@ -556,7 +560,7 @@ vegas_status configure(vegas_batch* b) {
   const gv::TileShape t = gv::choose_tile(b->threads, b->N, b->ppt_req, 1, occ_cap, occ_of, b->small_cap);
   BK(b, e);
   if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel does not fit: %d threads", b->threads);
-  b->smem = batch_smem(b->prec, b->N, t.cap);
+  b->smem = batch_smem(b->prec, b->maxd, b->N, t.cap);
   BK(b, gv_raise_smem_limit(b->kernel, b->smem));
   b->cap = t.cap;
   b->ppt = t.ppt;
@@ -573,6 +577,7 @@ BatchArgs batch_args(const vegas_batch* b, int refine, int record) {
   A.N = b->N;
   A.cap = b->cap;
   A.ppt = b->ppt;
+  A.maxd = b->maxd;
   A.key0 = (uint32_t)b->seed;
   A.key1 = (uint32_t)(b->seed >> 32);
   gv::philox_key_schedule(A.key0, A.key1, A.ks);
@@ -717,6 +722,7 @@ vegas_status vegas_batch_create(int n, const vegas_config* cfgs, const vegas_int
     const int d = cfgs[i].ndim;
     b->kind.push_back(fns[i].kind);
     b->d.push_back(d);
+    b->maxd = std::max(b->maxd, d);
     b->params.emplace_back(fns[i].params, fns[i].params + fns[i].nparams);
     double scale = 1.0;
     std::string why;

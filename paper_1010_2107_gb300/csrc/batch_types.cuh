@@ -37,6 +37,7 @@ struct BatchState {
 
 struct BatchArgs {
   int n, nitems, N, cap, ppt;
+  int maxd;  // widest instance (the general kernel's shared-memory layout)
   uint32_t key0, key1;
   uint32_t ks[kPhiloxKeyWords];  // Philox round keys of (key0, key1)
   const BatchInst* inst;

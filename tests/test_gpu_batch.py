@@ -246,3 +246,30 @@ def test_batch_set_params_matches_a_batch_created_with_them(gv, precision, ybits
             np.testing.assert_allclose(h1[1], h2[1], rtol=tol)
             np.testing.assert_allclose(gv.vegas_batch_get_grid(b1, i), gv.vegas_batch_get_grid(b2, i), rtol=0,
                                        atol=1e-12 if precision == 0 else 1e-5)
+
+
+def test_general_batch_kernel_layout_is_sized_for_the_widest_instance(gv, orc):
+    """The FP64 form (one kernel for every instance) sizes its shared memory
+    for the batch's widest instance: 256 bins fit up to ten axes (checked
+    against the oracle's first iteration, FP64 bars), while sixteen axes at
+    256 bins do not fit and the batch is refused at creation."""
+    rng = np.random.default_rng(7)
+    insts = [dict(kind=wl.GENZ_GAUSSIAN if d != 5 else wl.GENZ_CORNER_PEAK, ndim=d,
+                  params=_family_params(wl.GENZ_GAUSSIAN if d != 5 else wl.GENZ_CORNER_PEAK, d, rng),
+                  ncall=20_011 + d, instance=40 + d) for d in (2, 5, 10)]
+    with gv.vegas_batch_create(insts, nbins=256, precision=0, ybits=53, seed=3) as b:
+        gv.vegas_batch_iterate(b, 1)
+        for i, ins in enumerate(insts):
+            d = ins["ndim"]
+            cfg = orc.make_cfg(d, nbins=256, ncall=ins["ncall"], ybits=53, seed=3, instance=ins["instance"])
+            fn = orc.Integrand(ins["kind"], d, ins["params"])
+            o = orc.iteration(cfg, fn, orc.uniform_grid(d, 256), 0)
+            I, _ = gv.vegas_batch_get_history(b, i)[0]
+            _, bins = gv.vegas_batch_get_grid(b, i, bin_sums=True)
+            assert I == pytest.approx(o["I"], rel=1e-12)
+            assert np.all(np.abs(bins[0] - o["S1"]) <= 1e-12 * o["S1"][0].sum())
+            assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-12 * o["S2"][0].sum())
+    wide = [dict(kind=wl.GENZ_GAUSSIAN, ndim=16, params=_family_params(wl.GENZ_GAUSSIAN, 16, rng), ncall=5000,
+                 instance=1)]
+    with pytest.raises(gv.VegasError):
+        gv.vegas_batch_create(wide, nbins=256, precision=0, ybits=53, seed=3)
