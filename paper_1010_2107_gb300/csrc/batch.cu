@@ -919,7 +919,10 @@ vegas_status vegas_batch_set_params(vegas_batch* b, int first, int count, const 
     if (!gv::derive_params(b->kind[i], b->d[i], params + (size_t)j * stride, &dv[(size_t)j * K], &scale, &why))
       return b->fail(VEGAS_EINVAL, "instance %d: %s", i, why.c_str());
   }
-  if (!b->h_derived) BK(b, gv_malloc_host(&b->h_derived, b->derived.size() * sizeof(double)));
+  if (!b->h_derived && gv_malloc_host(&b->h_derived, b->derived.size() * sizeof(double)) != cudaSuccess) {
+    b->h_derived = nullptr;
+    return b->fail(VEGAS_ENOMEM, "cudaMallocHost failed (parameter staging)");
+  }
   BK(b, cudaStreamSynchronize(b->stream));  // the staging's previous upload has left it
   for (int j = 0; j < count; ++j) {
     const double* p = params + (size_t)j * stride;

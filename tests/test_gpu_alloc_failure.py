@@ -90,3 +90,24 @@ def test_failure_in_a_later_allocation_keeps_the_context_usable(gv):
         gv.vegas_fail_alloc_after(-1)
         r = gv.spring_generate(ctx, 0, 4096, events=False)
         assert r["n_events"] > 0
+
+
+def test_failed_parameter_staging_keeps_the_batch_usable(gv):
+    """vegas_batch_set_params allocates its pinned staging on first use: when
+    that allocation fails the call answers VEGAS_ENOMEM with the batch's
+    parameters unchanged, and the next call succeeds."""
+    insts = wl.genz_batch(8, seed=5, log2n_min=12, log2n_max=13)
+    with gv.vegas_batch_create(insts, nbins=50, seed=1, precision=gv.FP32_ACCCOMP, ybits=24) as b:
+        r0 = gv.vegas_batch_iterate(b, 1)
+        gv.vegas_fail_alloc_after(0)
+        with pytest.raises(gv.VegasError) as e:
+            gv.vegas_batch_set_params(b, [ins["params"] for ins in insts])
+        assert e.value.status == gv.ENOMEM
+        gv.vegas_fail_alloc_after(-1)
+        gv.vegas_batch_reset(b)
+        r1 = gv.vegas_batch_iterate(b, 1)
+        assert [r["I"] for r in r1] == [r["I"] for r in r0]  # parameters unchanged
+        gv.vegas_batch_set_params(b, [ins["params"] for ins in insts])
+        gv.vegas_batch_reset(b)
+        r2 = gv.vegas_batch_iterate(b, 1)
+        assert [r["I"] for r in r2] == [r["I"] for r in r0]
