@@ -460,11 +460,11 @@ vegas_status vegas_batch_get_launch(vegas_batch* batch, int* threads, int* round
 /* Histogram tile of the batched sampling kernels (as vegas_set_tile; no
  * counterpart in the paper): the points each thread evaluates between two
  * gathers of the CTA's buckets, 0 = automatic.  The FP32 form with 24-bit
- * words runs one kernel per dimension class (d <= 4, <= 8, <= 16), where
- * this is 1 or 2, the points a thread keeps in flight; the other forms
- * take 0..4.  EINVAL outside the range or when the tile does not fit (the
- * previous tile then stays).  get_tile returns the points per thread and
- * the bucket capacity (of the 16-axis class for the per-class kernels).
+ * words runs one kernel per dimension (d = 1..16), where this is 1 or 2,
+ * the points a thread keeps in flight; the other forms take 0..4.  EINVAL
+ * outside the range or when the tile does not fit (the previous tile then
+ * stays).  get_tile returns the points per thread and the bucket capacity
+ * (of the widest dimension's kernel for the per-dimension kernels).
  * Changes only speed and the summation order inside a CTA. */
 vegas_status vegas_batch_set_tile(vegas_batch* batch, int points_per_thread);
 vegas_status vegas_batch_get_tile(vegas_batch* batch, int* points_per_thread, int* cap);

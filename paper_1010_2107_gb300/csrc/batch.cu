@@ -33,12 +33,10 @@
 
 namespace gv {
 
-// Integrand dispatch for the batch: the family is uniform over an item.
-// KIND >= 0 fixes it at compile time; -1 switches per point.
-template <int KIND, typename T, int DM>
+// Integrand dispatch for the batch (the family is uniform over an item).
+template <typename T, int DM>
 __device__ __forceinline__ T batch_eval(int kind, const T (&x)[DM], int d, const T* P) {
-  const int k = KIND >= 0 ? KIND : kind;
-  switch (k) {
+  switch (kind) {
     case VG_GENZ_GAUSSIAN: return GenzGaussian<T, DM>::eval(x, d, P);
     case VG_GENZ_PRODUCT_PEAK: return GenzProductPeak<T, DM>::eval(x, d, P);
     case VG_GENZ_CORNER_PEAK: return GenzCornerPeak<T, DM>::eval(x, d, P);
@@ -49,9 +47,9 @@ __device__ __forceinline__ T batch_eval(int kind, const T (&x)[DM], int d, const
   }
 }
 
-// The points of one work item (all threads of the CTA): DMC bounds the
-// instance's dimension, KIND its family (-1: decided per point).
-template <typename T, int ACC, int YB, int DMC, int KIND>
+// The points of one work item (all threads of the CTA); DMC bounds the
+// instance's dimension.
+template <typename T, int ACC, int YB, int DMC>
 __device__ __forceinline__ void batch_item_points(const BatchArgs& B, const SampleArgs& A, const BatchItem& W,
                                                   int kind, uint32_t it, int d,
                                                   const typename Vec2<T>::type* tab, const T* P,
@@ -69,7 +67,7 @@ __device__ __forceinline__ void batch_item_points(const BatchArgs& B, const Samp
       T x[DMC];
       int kb[DMC];
       const T J = make_point<T, DMC, YB>(A, it, W.s0 + j, cd, tab, x, kb, nullptr);
-      T w = batch_eval<KIND, T, DMC>(kind, x, d, P) * J;
+      T w = batch_eval<T, DMC>(kind, x, d, P) * J;
       if (!vfinite(w)) {
         ++nonfinite;
         w = T(0);
@@ -154,18 +152,7 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
     const uint32_t it = B.st[W.inst].it;
     Run<ACC> sw, sw2;
     int nonfinite = 0;
-    if constexpr (std::is_same<T, float>::value && YB == 24) {
-      // loops sized by the dimension class (d <= 4, <= 8, <= 16); a
-      // compile-time family as well would cost registers (measured)
-      if (d <= 4)
-        batch_item_points<T, ACC, YB, 4, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
-      else if (d <= 8)
-        batch_item_points<T, ACC, YB, 8, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
-      else
-        batch_item_points<T, ACC, YB, DM, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
-    } else {
-      batch_item_points<T, ACC, YB, DM, -1>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
-    }
+    batch_item_points<T, ACC, YB, DM>(B, A, W, I.kind, it, d, tab, P, hist, sw, sw2, nonfinite);
     // the item's partial row: cells, then sum w, sum w^2, non-finite count
     for (int i = tid; i < 2 * dN; i += blockDim.x) {
       if constexpr (COMP) {
@@ -429,9 +416,11 @@ const void* batch_kernel() {
   return (const void*)&gv::k_batch_sample<T, ACC, YB>;
 }
 
+// The general kernel: FP64, or FP32 with 53-bit words (the FP32 form with
+// 24-bit words runs the per-dimension kernels instead).
 const void* pick_batch_kernel(int prec, int ybits) {
   if (prec == VG_FP64) return ybits == 24 ? batch_kernel<double, 0, 24>() : batch_kernel<double, 0, 53>();
-  return ybits == 24 ? batch_kernel<float, 2, 24>() : batch_kernel<float, 2, 53>();
+  return batch_kernel<float, 2, 53>();
 }
 
 size_t batch_smem(int prec, int md, int N, int cap) {
@@ -1019,7 +1008,7 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   };
   std::vector<Cand> cands;
   // one warm-up pass, then the mean of n passes, for shape (t, r), tile p
-  // (the per-class kernels: points in flight) and capacity policy `small`
+  // (the per-dimension kernels: points in flight) and capacity policy `small`
   auto time_shape = [&](int t, int r, int p, bool small, int n, double* out) -> vegas_status {
     b->small_cap = small;
     b->ppt_req = p;

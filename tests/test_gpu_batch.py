@@ -42,7 +42,7 @@ SMALL = [
 ]
 
 
-@pytest.mark.parametrize("precision,ybits,tol", [(0, 53, 1e-12), (2, 24, 1e-5)])
+@pytest.mark.parametrize("precision,ybits,tol", [(0, 53, 1e-12), (0, 24, 1e-12), (2, 24, 1e-5), (2, 53, 1e-5)])
 def test_batch_matches_standalone_contexts(gv, precision, ybits, tol):
     iters = 3
     with gv.vegas_batch_create(SMALL, precision=precision, ybits=ybits, seed=4) as b:
