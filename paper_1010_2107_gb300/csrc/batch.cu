@@ -342,6 +342,7 @@ struct vegas_batch {
   int threads = 256, rounds = 32, ctas = 0, cap = 16, ppt = 1, occ = 0;
   int ppt_req = 0;         // points per thread per tile asked for (0: automatic)
   bool small_cap = false;  // tile capacity policy (gv::choose_tile)
+  bool dense_cap = false;  // the dense floor of that policy (per-dimension kernels)
   // FP32 form with 24-bit words: one kernel per exact dimension d = 1..16,
   // each with its item range, tile and launch shape, run concurrently on
   // the auxiliary streams (forked from and joined to `stream`)
@@ -516,7 +517,7 @@ vegas_status configure_dims(vegas_batch* b) {
     };
     int occ_cap = 0;
     BK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_cap, c.fn, b->threads, 0));
-    const gv::TileShape t = gv::choose_tile(b->threads, b->N, pif, pif, occ_cap, occ_of, b->small_cap);
+    const gv::TileShape t = gv::choose_tile(b->threads, b->N, pif, pif, occ_cap, occ_of, b->small_cap, b->dense_cap);
     BK(b, e);
     if (t.occ < 1) return b->fail(VEGAS_EINVAL, "batch kernel for %d axes does not fit: %d threads", d, b->threads);
     c.cap = gv::DimSmem::stride(t.cap);  // the row holds this many slots
@@ -1002,15 +1003,17 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   static const int kThreads[] = {128, 256};
   static const int kRounds[] = {8, 16, 32, 64, 128};
   struct Cand {
-    int t, r, p;
-    bool small;
+    int t, r, p, pol;
     double ms;
   };
   std::vector<Cand> cands;
   // one warm-up pass, then the mean of n passes, for shape (t, r), tile p
-  // (the per-dimension kernels: points in flight) and capacity policy `small`
-  auto time_shape = [&](int t, int r, int p, bool small, int n, double* out) -> vegas_status {
-    b->small_cap = small;
+  // (the per-dimension kernels: points in flight) and capacity policy pol
+  // (0: the largest capacity of the range, 1: the smallest, 2: the dense
+  // floor, per-dimension kernels only)
+  auto time_shape = [&](int t, int r, int p, int pol, int n, double* out) -> vegas_status {
+    b->small_cap = pol >= 1;
+    b->dense_cap = pol == 2;
     b->ppt_req = p;
     vegas_status st = vegas_batch_set_launch(b, t, r);
     double m[2];
@@ -1024,13 +1027,13 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
     for (int r : kRounds)
       for (int p : tiles) {
         int cap_large = -1;  // a repeated tile is not timed twice
-        for (bool small : {false, true}) {
+        for (int pol = 0; pol < (b->by_dim ? 3 : 2); ++pol) {
           double m = 0.0;
-          vegas_status st = time_shape(t, r, p, small, 3, &m);
+          vegas_status st = time_shape(t, r, p, pol, 3, &m);
           if (st) return st;
-          if (small && b->cap == cap_large) continue;
-          if (!small) cap_large = b->cap;
-          cands.push_back({t, r, p, small, m});
+          if (pol == 1 && b->cap == cap_large) continue;
+          if (pol == 0) cap_large = b->cap;
+          cands.push_back({t, r, p, pol, m});
         }
       }
   // the three fastest again in interleaved rounds, keeping each one's best
@@ -1039,13 +1042,14 @@ vegas_status vegas_batch_autotune(vegas_batch* b, int* threads, int* rounds, dou
   for (int k = 0; k < 3; ++k)
     for (Cand& c : cands) {
       double m = 0.0;
-      vegas_status st = time_shape(c.t, c.r, c.p, c.small, 3, &m);
+      vegas_status st = time_shape(c.t, c.r, c.p, c.pol, 3, &m);
       if (st) return st;
       c.ms = k == 0 ? m : std::min(c.ms, m);
     }
   const Cand best = *std::min_element(cands.begin(), cands.end(),
                                       [](const Cand& a, const Cand& c) { return a.ms < c.ms; });
-  b->small_cap = best.small;
+  b->small_cap = best.pol >= 1;
+  b->dense_cap = best.pol == 2;
   b->ppt_req = best.p;
   vegas_status st = vegas_batch_set_launch(b, best.t, best.r);
   if (st) return st;

@@ -26,10 +26,11 @@
 // The scatter has no branch per axis: a claim past the capacity stores into
 // a junk word (never read) and sets a bit of the point's overflow mask;
 // after the point's axes, the rare overflowed ones go to their cells with
-// float atomics.  The cells hold FP32 (S1, S2) tile sums, folded into a
-// second FP32 pair every 16 tiles, so an item's cell carries at most
-// 16 + tiles/16 roundings of FP32 (1.4e-6 relative for 128 tiles); the item
-// row is written as an exact (hi, lo) pair of the two levels and the
+// float atomics.  The cells hold FP32 (S1, S2) tile sums, folded every 16
+// tiles into a second FP32 level kept in the item's own output row (global
+// memory, written by the one thread that owns the cell), so an item's cell
+// carries at most 16 + tiles/16 roundings of FP32 (1.4e-6 relative for 128
+// tiles); the row ends as the exact (hi, lo) pair of the two levels and the
 // finalisation merges rows compensated.  Per-thread sums of w and w^2 are
 // plain FP32 over 16 points, then merged into compensated pairs.
 #pragma once
@@ -95,27 +96,26 @@ __host__ __device__ inline int stream_scalar_base(int kind) {
 
 // Shared memory of k_batch_dim<D> with bucket capacity cap (cells = D N):
 // grid table, axis constants, scalars, the cells' claim counters, the
-// bucket rows, a junk word, then the cells' (S1, S2) tile sums and folds.
-// A bucket row is S words, S = cap rounded up to 4 (mod 8): an odd number
-// of 16-byte vectors, so that the rows of 32 consecutive cells start in all
-// eight vector positions of the 32 banks (conflict-free vector reads in the
-// gather, and slot stores spread over the banks).  Claims past the capacity
-// store into the junk word (never read).
+// bucket rows, a junk word, then the cells' (S1, S2) tile sums.  A bucket
+// row is S words, S the smallest value >= cap with S/2 odd: the gather
+// reads a row as 8-byte pairs, and with S/2 odd the rows of 16 consecutive
+// cells start on 16 different bank pairs (conflict-free reads).  Claims past
+// the capacity store into the junk word (never read).
 struct DimSmem {
   static __host__ __device__ size_t a16(size_t b) { return (b + 15) & ~size_t(15); }
   static __host__ __device__ int stride(int cap) {
-    const int r = (cap + 3) & ~3;
-    return r % 8 == 0 ? r + 4 : r;
+    int r = (cap + 1) & ~1;
+    return (r / 2) % 2 == 0 ? r + 2 : r;
   }
   static __host__ __device__ size_t off_pc(int cells) { return a16((size_t)cells * sizeof(float2)); }
   static __host__ __device__ size_t off_sc(int cells, int d) { return off_pc(cells) + a16((size_t)d * sizeof(float2)); }
   static __host__ __device__ size_t off_cnt(int cells, int d) { return a16(off_sc(cells, d) + 8 * sizeof(float)); }
   static __host__ __device__ size_t off_rows(int cells, int d) { return a16(off_cnt(cells, d) + (size_t)cells * sizeof(int)); }
   static __host__ __device__ size_t off_cells(int cells, int d, int cap) {
-    return off_rows(cells, d) + (size_t)cells * stride(cap) * sizeof(float) + 16;  // rows, junk word
+    return a16(off_rows(cells, d) + (size_t)cells * stride(cap) * sizeof(float) + sizeof(float));  // rows, junk
   }
   static __host__ __device__ size_t bytes(int cells, int d, int cap) {
-    return off_cells(cells, d, cap) + 2 * (size_t)cells * sizeof(float2);  // (S1, S2) tile sums, folds
+    return off_cells(cells, d, cap) + (size_t)cells * sizeof(float2);  // (S1, S2) tile sums
   }
 };
 
@@ -190,35 +190,36 @@ __device__ __forceinline__ void dim_scatter(int* cnt, float* rows, float* junk, 
 }
 
 // End of a tile (all threads): each cell's bucket into its FP32 (S1, S2)
-// tile sums (paired instructions), optionally folded into the item's second
-// level ff, and the counter reset.  Only the filled slots are read: whole
-// vectors, then the partial last one with its stale slots masked (the
-// slots are never cleared: shared-memory stores are the scarce resource).
-__device__ __forceinline__ void dim_gather(int* cnt, const float* rows, float2* cc, float2* ff, int dN, int S,
+// tile sums (paired instructions) and the counter reset; when `fold`, the
+// tile sums move into the second level, the .x words of the cell's two
+// entries in the item row (S1 at cell, S2 at dN + cell), which only this
+// thread touches until the row is finished.  Only the filled slots are
+// read: whole pairs, then a last odd slot (the slots are never cleared:
+// shared-memory stores are the scarce resource).
+__device__ __forceinline__ void dim_gather(int* cnt, const float* rows, float2* cc, float2* row, int dN, int S,
                                            int cap, bool fold) {
   __syncthreads();
   for (int cell = threadIdx.x; cell < dN; cell += blockDim.x) {
     const int n = min(cnt[cell], cap);
-    const float4* row = reinterpret_cast<const float4*>(rows + cell * S);
+    const float2* r2 = reinterpret_cast<const float2*>(rows + cell * S);
     float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-    auto add = [&](const float4 v) {
-      const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
-      s1 = __fadd2_rn(s1, __fadd2_rn(lo, hi));
-      s2 = __ffma2_rn(lo, lo, s2);
-      s2 = __ffma2_rn(hi, hi, s2);
-    };
-    const int nf = n >> 2, r = n & 3;
-    for (int q = 0; q < nf; ++q) add(row[q]);
-    if (r) {
-      const float4 v = row[nf];
-      add(make_float4(v.x, r > 1 ? v.y : 0.f, r > 2 ? v.z : 0.f, 0.f));
+    const int np = n >> 1;
+    for (int q = 0; q < np; ++q) {
+      const float2 v = r2[q];
+      s1 = __fadd2_rn(s1, v);
+      s2 = __ffma2_rn(v, v, s2);
+    }
+    if (n & 1) {
+      const float v = rows[cell * S + n - 1];
+      s1.x += v;
+      s2.x = fmaf(v, v, s2.x);
     }
     float2 c = cc[cell];
     c.x += s1.x + s1.y;
     c.y += s2.x + s2.y;
     if (fold) {
-      const float2 f = ff[cell];
-      ff[cell] = make_float2(f.x + c.x, f.y + c.y);
+      row[cell].x += c.x;
+      row[dN + cell].x += c.y;
       c = make_float2(0.f, 0.f);
     }
     cc[cell] = c;
@@ -232,7 +233,7 @@ __device__ __forceinline__ void dim_gather(int* cnt, const float* rows, float2* 
 template <int D, int PIF, int KIND>
 __device__ __forceinline__ void dim_item(const BatchArgs& B, const BatchItem& W, uint32_t it, uint32_t inst, int N,
                                          float2 npw, const float2* tab, const float2* pc, const float* sc, int* cnt,
-                                         float* rows, float* junk, float2* cc, float2* ff, int S, int cap, fpair& sw,
+                                         float* rows, float* junk, float2* cc, float2* row, int S, int cap, fpair& sw,
                                          fpair& sw2, int& nonfinite) {
   const int tid = threadIdx.x, T = blockDim.x, dN = D * N;
   const uint32_t rounds = (W.count + T - 1) / T;
@@ -265,7 +266,7 @@ __device__ __forceinline__ void dim_item(const BatchArgs& B, const BatchItem& W,
       p1 = p2 = 0.f;
       since = 0;
     }
-    dim_gather(cnt, rows, cc, ff, dN, S, cap, ++tiles % kFoldTiles == 0);
+    dim_gather(cnt, rows, cc, row, dN, S, cap, ++tiles % kFoldTiles == 0);
   }
   comp_add(sw, p1);
   comp_add(sw2, p2);
@@ -288,7 +289,6 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
   float* rows = reinterpret_cast<float*>(smem + DimSmem::off_rows(cells, D));
   float* junk = rows + (size_t)cells * S;
   float2* cc = reinterpret_cast<float2*>(smem + DimSmem::off_cells(cells, D, cap));
-  float2* ff = cc + cells;
   __shared__ int s_item;
   __shared__ fpair red_p[8][2];
   __shared__ int red_n[8];
@@ -314,9 +314,13 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
       if (tid < 8) sc[tid] = base >= 0 ? (float)dp[base + tid] : 0.f;
       cur = W.inst;
     }
+    // the item's row: its cells' .x words hold the folded level until the
+    // row is finished (each by the thread that owns the cell)
+    float2* row = reinterpret_cast<float2*>(B.rows) + W.row;
     for (int i = tid; i < cells; i += blockDim.x) {
       cc[i] = make_float2(0.f, 0.f);
-      ff[i] = make_float2(0.f, 0.f);
+      row[i].x = 0.f;
+      row[cells + i].x = 0.f;
     }
     // N^4 and N^(D mod 4) for the Jacobian
     const float Nf = (float)N, N2 = Nf * Nf;
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
     fpair sw{0.f, 0.f}, sw2{0.f, 0.f};
     int nonfinite = 0;
 #define GV_DIM_ITEM(K) \
-  dim_item<D, PIF, K>(B, W, it, I.instance, N, npw, tab, pc, sc, cnt, rows, junk, cc, ff, S, cap, sw, sw2, nonfinite)
+  dim_item<D, PIF, K>(B, W, it, I.instance, N, npw, tab, pc, sc, cnt, rows, junk, cc, row, S, cap, sw, sw2, nonfinite)
     switch (I.kind) {
       case VG_GENZ_GAUSSIAN: GV_DIM_ITEM(VG_GENZ_GAUSSIAN); break;
       case VG_GENZ_PRODUCT_PEAK: GV_DIM_ITEM(VG_GENZ_PRODUCT_PEAK); break;
@@ -340,13 +344,12 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
 #undef GV_DIM_ITEM
     // the item's row, S1 cells then S2 cells, each the exact pair of its
     // two FP32 levels
-    float2* row = reinterpret_cast<float2*>(B.rows) + W.row;
     for (int i = tid; i < cells; i += blockDim.x) {
-      const float2 f = ff[i], c = cc[i];
+      const float2 c = cc[i];
       float hi, lo;
-      two_sum(f.x, c.x, hi, lo);
+      two_sum(row[i].x, c.x, hi, lo);
       row[i] = make_float2(hi, lo);
-      two_sum(f.y, c.y, hi, lo);
+      two_sum(row[cells + i].x, c.y, hi, lo);
       row[cells + i] = make_float2(hi, lo);
     }
     const fpair a = warp_sum(sw), b = warp_sum(sw2);

@@ -93,10 +93,12 @@ struct TileShape {
 // occ_of(cap, ppt) returns the CTAs per SM (0: does not fit).  With
 // `small_cap` the smallest capacity of the range that reaches the best
 // occupancy is taken (less to gather, more claims spilling past the
-// buckets), else the largest.
+// buckets), else the largest.  `dense` lowers the range's floor to
+// m + sqrt(m) + 1 (a few percent of the claims spill), for kernels whose
+// shared memory is what holds the CTAs per SM down.
 template <class OccOf>
 inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int occ_cap, OccOf occ_of,
-                             bool small_cap = false) {
+                             bool small_cap = false, bool dense = false) {
   auto ceil4 = [](double v) { return ((int)v + 1 + 3) & ~3; };
   TileShape best{0, 0, 0};
   const int wanted = occ_cap * threads / 32 < 16 ? occ_cap * threads / 32 : 16;
@@ -106,7 +108,7 @@ inline TileShape choose_tile(int threads, int N, int ppt_req, int ppt_min, int o
     if (ppt_req <= 0 && cands[i] < ppt_min) continue;
     const int ppt = ppt_req > 0 ? ppt_req : cands[i];
     const double m = (double)threads * ppt / N;
-    int hi = ceil4(m + 4.0 * __builtin_sqrt(m) + 2.0), lo = ceil4(m + 2.0 * __builtin_sqrt(m) + 1.0);
+    int hi = ceil4(m + 4.0 * __builtin_sqrt(m) + 2.0), lo = ceil4(m + (dense ? 1.0 : 2.0) * __builtin_sqrt(m) + 1.0);
     hi = hi > 64 ? 64 : hi;
     lo = lo > hi ? hi : lo;
     TileShape t{ppt, hi, 0};
