@@ -166,17 +166,34 @@ __device__ __forceinline__ float dim_point(const BatchArgs& B, uint32_t s, uint3
 
 // Bucket scatter of one point's weight into its D cells (cnt: the claim
 // counters; rows: the bucket rows; cc: the cells' (S1, S2) tile sums).
+// The claims of a group of axes are issued together, then their stores:
+// a store may alias a later claim's counter as far as the compiler knows,
+// so claim-store pairs in sequence would expose every claim's latency.
 template <int D>
 __device__ __forceinline__ void dim_scatter(int* cnt, float* rows, float* junk, float2* cc, int N, int S, int cap,
                                             const uint32_t (&kb)[(D + 3) / 4], float w) {
+  constexpr int G = D < 8 ? D : 8;  // axes per group of claims
   uint32_t ovf = 0u;
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const int cell = a * N + (int)__byte_perm(kb[a >> 2], 0u, 0x4440u | (unsigned)(a & 3));
-    const int pos = atomicAdd(&cnt[cell], 1);
-    const bool over = pos >= cap;
-    *(over ? junk : rows + cell * S + pos) = w;
-    if (over) ovf |= 1u << a;
+  for (int a0 = 0; a0 < D; a0 += G) {
+    int cell[G], pos[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int a = a0 + g;
+      if (a < D) {
+        cell[g] = a * N + (int)__byte_perm(kb[a >> 2], 0u, 0x4440u | (unsigned)(a & 3));
+        pos[g] = atomicAdd(&cnt[cell[g]], 1);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int a = a0 + g;
+      if (a < D) {
+        const bool over = pos[g] >= cap;
+        *(over ? junk : rows + cell[g] * S + pos[g]) = w;
+        if (over) ovf |= 1u << a;
+      }
+    }
   }
   if (ovf) {  // claims past the capacity (rare): straight to the cells
 #pragma unroll

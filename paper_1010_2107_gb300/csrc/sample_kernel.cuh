@@ -260,18 +260,27 @@ struct TileHist {
       if (COMP) cmp[i] = fpair{0.f, 0.f};
     }
   }
+  // The claims of a group of axes are issued together, then their stores
+  // (a store may alias a later claim's counter as far as the compiler
+  // knows: claim-store pairs in sequence would expose every claim's
+  // latency).
   template <int DM>
   __device__ __forceinline__ void scatter(const int (&kb)[DM], int d, H w) {
+    constexpr int G = DM < 8 ? DM : 8;
     int pos[DM];
     int top = 0;
 #pragma unroll
-    for (int a = 0; a < DM; ++a)
-      if (a < d) {
-        const int cell = a * N + kb[a];
-        pos[a] = atomicAdd(&cnt[cell], 1);
-        bucket[cell * S + min(pos[a], cap)] = w;
-        top = max(top, pos[a]);
-      }
+    for (int a0 = 0; a0 < DM; a0 += G) {
+#pragma unroll
+      for (int a = a0; a < a0 + G && a < DM; ++a)
+        if (a < d) pos[a] = atomicAdd(&cnt[a * N + kb[a]], 1);
+#pragma unroll
+      for (int a = a0; a < a0 + G && a < DM; ++a)
+        if (a < d) {
+          bucket[(a * N + kb[a]) * S + min(pos[a], cap)] = w;
+          top = max(top, pos[a]);
+        }
+    }
     if (__builtin_expect(top >= cap, 0)) {
       // spare-slot claims: add to the cells directly (nothing reads them
       // before the gather's barrier)
