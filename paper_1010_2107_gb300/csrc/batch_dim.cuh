@@ -332,12 +332,14 @@ __global__ void __launch_bounds__(256, kDimMinBlocks<D>) k_batch_dim(const Batch
       cur = W.inst;
     }
     // the item's row: its cells' .x words hold the folded level until the
-    // row is finished (each by the thread that owns the cell)
+    // row is finished (each by the thread that owns the cell); cleared as
+    // whole pairs, so that every 32-byte sector is written in full and L2
+    // need not fetch it from memory
     float2* row = reinterpret_cast<float2*>(B.rows) + W.row;
     for (int i = tid; i < cells; i += blockDim.x) {
       cc[i] = make_float2(0.f, 0.f);
-      row[i].x = 0.f;
-      row[cells + i].x = 0.f;
+      row[i] = make_float2(0.f, 0.f);
+      row[cells + i] = make_float2(0.f, 0.f);
     }
     // N^4 and N^(D mod 4) for the Jacobian
     const float Nf = (float)N, N2 = Nf * Nf;
