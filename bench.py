@@ -65,10 +65,10 @@ ALGO_OPS = {
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/), per pass kind (refining, frozen grid); a workload
 # whose kernel changed since its capture has no entry.
-TRAFFIC = {"dgauss8": (84864, 615424), "rambo5": (113792,), "wmunu": (80896, 352384),
+TRAFFIC = {"dgauss8": (86528, 614272), "rambo5": (122112,), "wmunu": (80896, 352384),
            "rambo4_adjoint": (64256,), "spring_dgauss8": (1016320 + 3025408,),
            # one batched pass: the sum over its fifteen dimension kernels
-           "genz256": (3019776,)}
+           "genz256": (3666688,)}
 
 
 def _workload(name):
