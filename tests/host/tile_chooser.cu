@@ -18,7 +18,7 @@ int main() {
         for (int reg_cap : {1, 2, 4})
           for (int ppt_req : {0, 1, 2, 4})
             for (int ppt_min : {1, 2})
-              for (int small : {0, 1}) {
+              for (int small : {0, 1, 2}) {  // 2: the small policy with the dense floor
                 // model: 227 KB per SM, bytes = dN (cap + 4) 4 + 8 dN
                 auto occ_of = [&](int cap, int) {
                   const long bytes = (long)dN * (cap + 4) * 4 + 8L * dN;
@@ -27,7 +27,7 @@ int main() {
                   return o < reg_cap ? o : reg_cap;
                 };
                 const gv::TileShape t =
-                    gv::choose_tile(threads, N, ppt_req, ppt_min, reg_cap, occ_of, small != 0);
+                    gv::choose_tile(threads, N, ppt_req, ppt_min, reg_cap, occ_of, small != 0, small == 2);
                 std::printf("%s{\"threads\":%d,\"N\":%d,\"dN\":%d,\"reg_cap\":%d,\"ppt_req\":%d,\"ppt_min\":%d,"
                             "\"small\":%d,\"ppt\":%d,\"cap\":%d,\"occ\":%d,\"occ_check\":%d}\n",
                             first ? "" : ",", threads, N, dN, reg_cap, ppt_req, ppt_min, small, t.ppt, t.cap, t.occ,

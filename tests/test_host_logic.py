@@ -6,7 +6,8 @@ compiled for the host and run without a GPU against a model of occupancy:
   reported occupancy the model's for that capacity, and with the small
   policy no smaller capacity of the searched range reaching the same
   occupancy; the large policy never takes a smaller capacity than the
-  small one for the same tile;
+  small one for the same tile; the dense floor never loses occupancy
+  against the small policy;
 * lanes: a power of two, at most 32 and at most the points per hypercube,
   the smallest that gives four rounds of work (or the bound).
 """
@@ -60,6 +61,31 @@ def test_small_policy_takes_the_smallest_capacity_of_equal_occupancy(run):
         big, small = pair[0], pair[1]
         if big["ppt"] == small["ppt"] and big["occ"] == small["occ"] and big["occ"] > 0:
             assert small["cap"] <= big["cap"], (big, small)
+
+
+def test_dense_floor_never_loses_occupancy(run):
+    """The dense floor extends the small policy's range downwards: for the
+    same tile it reaches at least the small policy's occupancy, and where
+    the small policy found its capacity inside its own range (not by the
+    halving fallback of a forced tile), never a larger one."""
+    import math
+    tiles, _ = run
+    key = lambda t: (t["threads"], t["N"], t["dN"], t["reg_cap"], t["ppt_req"], t["ppt_min"])
+    ceil4 = lambda v: (int(v) + 1 + 3) & ~3
+    by = {}
+    for t in tiles:
+        by.setdefault(key(t), {})[t["small"]] = t
+    checked = 0
+    for k, trio in by.items():
+        small, dense = trio[1], trio[2]
+        if small["ppt"] == dense["ppt"] and small["occ"] > 0:
+            assert dense["occ"] >= small["occ"], (small, dense)
+            m = small["threads"] * small["ppt"] / small["N"]
+            lo_small = min(ceil4(m + 2 * math.sqrt(m) + 1), min(ceil4(m + 4 * math.sqrt(m) + 2), 64))
+            if dense["occ"] == small["occ"] and small["cap"] >= lo_small:
+                assert dense["cap"] <= small["cap"], (small, dense)
+            checked += 1
+    assert checked > 100
 
 
 def test_lanes(run):
