@@ -65,10 +65,10 @@ ALGO_OPS = {
 # DRAM bytes per launch of the sampling kernel from the committed ncu
 # capture (profiles/), per pass kind (refining, frozen grid); a workload
 # whose kernel changed since its capture has no entry.
-TRAFFIC = {"dgauss8": (86528, 614272), "rambo5": (122112,), "wmunu": (80640, 352256),
-           "rambo4_adjoint": (64256,), "spring_dgauss8": (1016320 + 3025408,),
+TRAFFIC = {"dgauss8": (83968, 614528), "rambo5": (108032,), "wmunu": (80896, 352512),
+           "rambo4_adjoint": (45504,), "spring_dgauss8": (1017088 + 3060992,),
            # one batched pass: the sum over its fifteen dimension kernels
-           "genz256": (3666688,)}
+           "genz256": (3620992,)}
 
 
 def _workload(name):
