@@ -207,21 +207,63 @@ __global__ void __launch_bounds__(256) k_batch_sample(const BatchArgs B) {
   }
 }
 
-// Sum of entry `off` over an instance's item rows, in item order.
-__device__ inline double row_sum(const BatchArgs& B, const BatchInst& I, int off) {
+// Sums of the entries off[0..K) over an instance's item rows, each in item
+// order.  The rows of an instance's items are consecutive, 2 d N + kRowTail
+// entries apart, so the addresses need no lookup: eight rows' loads are
+// issued ahead of their merges, which keep the sequential order.
+template <int K>
+__device__ inline void row_sums(const BatchArgs& B, const BatchInst& I, const int (&off)[K], double (&out)[K]) {
+  constexpr int U = 8;
+  const int n = I.nitems;
+  const size_t stride = 2 * (size_t)I.d * B.N + kRowTail, base = B.items[I.first_item].row;
   if (B.pair32) {
-    const float2* rows = reinterpret_cast<const float2*>(B.rows);
-    fpair acc{0.f, 0.f};
-    for (int k = 0; k < I.nitems; ++k) {
-      const float2 v = rows[B.items[I.first_item + k].row + off];
-      comp_merge(acc, fpair{v.x, v.y});
+    const float2* rows = reinterpret_cast<const float2*>(B.rows) + base;
+    fpair acc[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] = fpair{0.f, 0.f};
+    int k = 0;
+    for (; k + U <= n; k += U) {
+      float2 v[U][K];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < K; ++j) v[u][j] = rows[(size_t)(k + u) * stride + off[j]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < K; ++j) comp_merge(acc[j], fpair{v[u][j].x, v[u][j].y});
     }
-    return comp_value(acc);
+    for (; k < n; ++k)
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const float2 v = rows[(size_t)k * stride + off[j]];
+        comp_merge(acc[j], fpair{v.x, v.y});
+      }
+#pragma unroll
+    for (int j = 0; j < K; ++j) out[j] = comp_value(acc[j]);
+    return;
   }
-  const double* rows = reinterpret_cast<const double*>(B.rows);
-  double acc = 0.0;
-  for (int k = 0; k < I.nitems; ++k) acc += rows[B.items[I.first_item + k].row + off];
-  return acc;
+  const double* rows = reinterpret_cast<const double*>(B.rows) + base;
+  double acc[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) acc[j] = 0.0;
+  int k = 0;
+  for (; k + U <= n; k += U) {
+    double v[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < K; ++j) v[u][j] = rows[(size_t)(k + u) * stride + off[j]];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc[j] += v[u][j];
+  }
+  for (; k < n; ++k)
+#pragma unroll
+    for (int j = 0; j < K; ++j) acc[j] += rows[(size_t)k * stride + off[j]];
+#pragma unroll
+  for (int j = 0; j < K; ++j) out[j] = acc[j];
 }
 
 // Blocks [0, naxes): reduce one axis of one instance (2 N cells) and refine
@@ -235,10 +277,12 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
     const BatchInst I = B.inst[ia.x];
     const int N = B.N, a = ia.y, dN = I.d * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      const double S1 = row_sum(B, I, a * N + k), S2 = row_sum(B, I, dN + a * N + k);
-      B.bins[I.bins_off + a * N + k] = S1;
-      B.bins[I.bins_off + dN + a * N + k] = S2;
-      s2[k] = S2;
+      const int off[2] = {a * N + k, dN + a * N + k};
+      double S[2];
+      row_sums<2>(B, I, off, S);
+      B.bins[I.bins_off + a * N + k] = S[0];
+      B.bins[I.bins_off + dN + a * N + k] = S[1];
+      s2[k] = S[1];
     }
     __syncthreads();
     const Team t{min((int)blockDim.x, (N + 31) / 32 * 32)};  // one thread per bin, whole warps
@@ -252,8 +296,10 @@ __global__ void __launch_bounds__(128) k_batch_finalize(const BatchArgs B) {
   const bool w0 = threadIdx.x == 0;
   const BatchInst I = B.inst[i];
   const int dN = I.d * B.N;
-  const double sw = row_sum(B, I, 2 * dN), sw2 = row_sum(B, I, 2 * dN + 1);
-  const double nf = row_sum(B, I, 2 * dN + 2);
+  const int off[3] = {2 * dN, 2 * dN + 1, 2 * dN + 2};
+  double tot[3];
+  row_sums<3>(B, I, off, tot);
+  const double sw = tot[0], sw2 = tot[1], nf = tot[2];
   const double n = (double)I.ncall;
   const double Ij = sw / n;
   double var = (sw2 / n - Ij * Ij) / (n - 1.0);
