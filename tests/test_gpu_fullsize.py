@@ -13,7 +13,14 @@ refined grid; the full-iteration estimate against the oracle on the first
 rambo4_adjoint (2^24 points): the FP64 gradient against common-random-number
 central differences of the FP64 estimate (1e-3; FP32 cannot resolve
 M^2/s to the step size), and the FP32 gradient against the FP64 one on
-the same points and grid (1e-3)."""
+the same points and grid within 1e-4 of the mean |J df/dtheta| (the
+condition-scaled FP32 bar of the small-case gradient parity: the M and
+Gamma derivatives change sign across the Breit-Wigner peak, so their sums
+cancel) plus what the points that may fall on the other side of the hard
+Delta R cut can carry: a point whose oracle cut margin is below 1e-4 may
+be cut in one precision and kept in the other (the reading of the point
+parity), so the sum of |J df/dtheta| / n over those points, each taken
+without the cut, is allowed on top.  The oracle scans all 2^24 points."""
 import math
 
 import numpy as np
@@ -139,17 +146,34 @@ def test_rambo5_full_iteration_in_the_tuned_shape(gv, orc):
     assert np.all(np.abs(bins[1] - o["S2"]) <= 1e-5 * tot2 + 2e-4 * o["S2"])
 
 
-def test_rambo4_adjoint_full_size(gv):
+def test_rambo4_adjoint_full_size(gv, orc):
     w = wl.WORKLOADS["rambo4_adjoint"]
     params = np.asarray(w["params"], dtype=np.float64)
     with _ctx(gv, w) as c32:
         gv.vegas_iterate(c32, w["warmup_iters"], refine=True)
         edges = gv.vegas_get_grid(c32)
         g32, _ = gv.vegas_grad(c32, 100)
+    # the same points by the oracle: mean |J df/dtheta| and, for the points
+    # within the FP32 cut margin, |J df/dtheta| without the Delta R cut
+    cfg = orc.make_cfg(w["ndim"], nbins=w["nbins"], ncall=w["ncall"], ybits=w["ybits"], seed=w["seed"])
+    fn = orc.Integrand(w["kind"], w["ndim"], params)
+    p_nocut = params.copy()
+    p_nocut[wl.RB_DRMIN] = 0.0
+    fn_nocut = orc.Integrand(w["kind"], w["ndim"], p_nocut)
+    total = np.zeros(3)
+    flips = np.zeros(3)
+    chunk = 1 << 20
+    for c0 in range(0, w["ncall"], chunk):
+        p = orc.sample_batch(cfg, edges, 100, np.arange(c0, min(c0 + chunk, w["ncall"])))
+        total += np.abs(orc.integrand_grad(fn, p["x"]) * p["jac"][:, None]).sum(axis=0)
+        near = orc.cut_margin(fn, p["x"]) < 1e-4
+        if near.any():
+            flips += np.abs(orc.integrand_grad(fn_nocut, p["x"][near]) * p["jac"][near, None]).sum(axis=0)
+    scale, allow = total / w["ncall"], flips / w["ncall"]
     with _ctx(gv, dict(w, precision="fp64")) as ctx:
         gv.vegas_set_grid(ctx, edges)
         g, I = gv.vegas_grad(ctx, 100)
-        np.testing.assert_allclose(g32, g, rtol=1e-3)
+        assert np.all(np.abs(g32 - g) <= 1e-4 * scale + allow), (g32, g, scale, allow)
         for j, (slot, h) in enumerate(((wl.RB_M, 1e-3), (wl.RB_GAMMA, 1e-3), (wl.RB_T, 1e-2))):
             pp, pm = params.copy(), params.copy()
             pp[slot] += h
