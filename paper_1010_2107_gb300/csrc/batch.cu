@@ -494,6 +494,9 @@ vegas_status build_items(vegas_batch* b) {
       auto& c = b->dims[I.d - 1];
       if (c.count == 0) c.first = (int)b->items.size();
     }
+    // an instance's items are consecutive and so are their rows, each
+    // 2 d N + kRowTail entries long: k_batch_finalize addresses them by
+    // that stride from the first item's row
     I.first_item = (int)b->items.size();
     const uint64_t n = (uint64_t)b->cfg[i].ncall;
     for (uint64_t s0 = 0; s0 < n; s0 += tile) {
